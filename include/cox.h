@@ -1,0 +1,211 @@
+/*
+ * cox.h -- C ABI of the GB300 warp-collective library (libcox.so).
+ *
+ * The library runs CUDA warp-level functions -- shuffles, votes, match_any and
+ * cooperative-groups tiles of width 2..32 -- across whole grids, and the
+ * compositions built from them: tile and block reductions, tile inclusive
+ * scans, ballot-driven stable compaction and match-based histograms.  The
+ * paper (arXiv 2112.10034, COX) defines these functions' semantics by running
+ * CUDA kernels that use them on CPUs (Section 2.2.1 "Warp-level collectives",
+ * Section 4.2 "Support warp-level functions"); this library runs them on the
+ * GPU as hand-written sm_103a kernels.
+ *
+ * Conventions for every call below:
+ *   - d_* pointers are DEVICE pointers owned by the caller; the library keeps
+ *     no reference to them after the call returns.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL means
+ *     the legacy default stream).  Errors found on the host (bad arguments, a
+ *     failed launch) are returned at once and nothing is enqueued.  Errors
+ *     found on the device (a bounded wait that ran out) are recorded in a
+ *     device-side status word that cox_device_status() reads.
+ *   - The element of index i is the operand of global thread i: lane i % 32
+ *     of its warp and rank i % width of its width-`width` tile (Code 3's lane
+ *     numbering, Section 2.3).  `width` must be 2, 4, 8, 16 or 32.
+ *     `block_dim` (threads per block) must be a multiple of 32 in [32, 1024];
+ *     it defines the BLOCK scope and is otherwise a launch choice.
+ *   - Only full-tile masks are supported: the paper's translator covers
+ *     warp functions without divergence only (Section 2.2.3); a call whose
+ *     `mask` is not the full mask returns COX_EUNSUPPORTED.
+ *   - Ragged tails: lanes whose index is >= n take part as padding -- the
+ *     identity of the op, a false predicate, no histogram contribution -- and
+ *     nothing is written at an output index that has no input.
+ *   - Integer arithmetic wraps modulo 2^32.  fp32 sums round to nearest; the
+ *     COMPENSATED flag carries a TwoSum error term next to every partial sum.
+ *   - No call allocates device or host memory, and no call synchronises the
+ *     stream, except cox_device_status().
+ */
+#ifndef COX_H_
+#define COX_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  COX_OK = 0,
+  COX_EINVAL = 1,        /* bad argument: null pointer, bad width/block_dim/op/dtype, n < 0 */
+  COX_EUNSUPPORTED = 2,  /* valid request outside the supported scope (partial masks, ...) */
+  COX_ECUDA = 3,         /* a CUDA runtime call or launch failed */
+  COX_ENOMEM = 4,        /* workspace or budget too small */
+  COX_ETIMEOUT = 5,      /* a bounded device-side wait ran out (cox_device_status) */
+  COX_EBUSY = 6          /* resource in use (server: no free slot) */
+} cox_status;
+
+typedef enum { COX_I32 = 0, COX_U32 = 1, COX_F32 = 2 } cox_dtype;
+
+typedef enum { COX_SUM = 0, COX_MIN = 1, COX_MAX = 2, COX_AND = 3, COX_OR = 4, COX_XOR = 5 } cox_op;
+
+typedef enum {
+  COX_SHFL_IDX = 0,  /* __shfl_sync(mask, v, srcLane, width) */
+  COX_SHFL_UP = 1,   /* __shfl_up_sync(mask, v, delta, width) */
+  COX_SHFL_DOWN = 2, /* __shfl_down_sync(mask, v, delta, width) */
+  COX_SHFL_XOR = 3,  /* __shfl_xor_sync(mask, v, laneMask, width) */
+  COX_BALLOT = 4,    /* tile.ballot(v != 0): tile-local mask */
+  COX_ANY = 5,       /* tile.any(v != 0) */
+  COX_ALL = 6,       /* tile.all(v != 0) */
+  COX_MATCH_ANY = 7  /* tile.match_any(v): tile-local mask of equal lanes */
+} cox_warpfn;
+
+typedef enum { COX_SCOPE_TILE = 0, COX_SCOPE_BLOCK = 1, COX_SCOPE_GRID = 2 } cox_scope;
+
+enum {
+  COX_F_COMPENSATED = 1u,  /* fp32 sums: TwoSum-compensated pairs through every stage */
+  COX_F_FP64_COMBINE = 2u, /* GRID scope fp32 sum: final cross-block combine in FP64 */
+  COX_F_WS_READY = 4u      /* compaction: caller zeroed the workspace; skip the memset */
+};
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* cox_status_string(cox_status s);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int cox_version(void);
+
+/*
+ * cox_shfl -- one warp function on every lane of a 1-D grid.
+ *
+ * Section 2.2.1 (warp shuffle, warp vote), Code 1 (shfl_down), Code 4
+ * (__all_sync); semantics are PTX shfl.sync / vote.sync / match.sync at
+ * segment width `width`.
+ *   d_in   n elements of dt (32-bit each).  Votes use the predicate v != 0
+ *          (for F32: the value compared with 0.0f); MATCH_ANY compares bits.
+ *   d_out  n elements.  Shuffles: dt, the source lane's bits (0 when the
+ *          source lane is padding); BALLOT/MATCH_ANY: uint32 tile-local masks
+ *          (bit r <-> tile rank r); ANY/ALL: int32 0 or 1.
+ *   param  srcLane (IDX; taken modulo width), delta (UP/DOWN, 0..31) or
+ *          laneMask (XOR, 0..31; may name lanes of earlier tiles of the same
+ *          warp, per PTX); ignored by votes and match.
+ *   mask   must be 0xFFFFFFFF (COX_EUNSUPPORTED otherwise).
+ */
+cox_status cox_shfl(cox_warpfn fn, cox_dtype dt, int width, int block_dim, const void* d_in,
+                    void* d_out, int64_t n, int param, uint32_t mask, void* stream);
+
+/*
+ * cox_tile_reduce -- reductions over tiles, blocks or the whole grid.
+ *
+ * Code 1 of the paper (a shfl_down tree into lane 0, Section 2.3) and the SDK
+ * reduction kernels of Table 1 (reduce0..reduce6, reduce, reduceFinal).
+ *   scope TILE:  d_out[t] = x[t*width] op ... op x[t*width + width - 1],
+ *                ceil(n / width) outputs.
+ *   scope BLOCK: d_out[b] = reduction of x[b*block_dim .. +block_dim),
+ *                ceil(n / block_dim) outputs.  Order: width-`width` shfl_down
+ *                tree per tile; tile partials to shared memory; warp 0 lane l
+ *                folds partials l, l+32, ... then a width-32 shfl_down tree.
+ *   scope GRID:  d_out[0] = reduction of all n elements (0 elements: identity).
+ *                Needs d_workspace of cox_tile_reduce_workspace() bytes.
+ *   op/dt: SUM/MIN/MAX/AND/OR/XOR for I32 and U32; SUM/MIN/MAX for F32.
+ *   flags: COX_F_COMPENSATED (F32 SUM only): TwoSum pairs through the tree
+ *          and the combine; the output is fl(s + e).  COX_F_FP64_COMBINE
+ *          (GRID, F32 SUM): the final combine of block partials in FP64.
+ *   d_err: optional (may be NULL); with COX_F_COMPENSATED, receives for each
+ *          output the low word lo such that out + lo == s + e exactly.
+ *   d_workspace / workspace_bytes: scratch for GRID scope (ignored otherwise;
+ *          may be NULL).  Contents need no initialisation; not shared across
+ *          concurrent calls.
+ * TILE and BLOCK results are reproducible bit for bit: fp32 values follow the
+ * stated order exactly, with no fused operations.
+ */
+cox_status cox_tile_reduce(cox_op op, cox_dtype dt, int width, int block_dim, cox_scope scope,
+                           const void* d_in, void* d_out, int64_t n, unsigned flags, void* d_err,
+                           void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* Workspace bytes cox_tile_reduce needs for `scope` (0 for TILE and BLOCK). */
+size_t cox_tile_reduce_workspace(cox_scope scope, int64_t n, int block_dim);
+
+/*
+ * cox_tile_scan -- inclusive scan within each tile of `width` elements.
+ *
+ * The shuffle scan of the SDK's shfl_scan_test (Table 1) on a
+ * cooperative-groups tile: for d = 1, 2, .., width/2: u = shfl_up(x, d);
+ * if (rank >= d) x = u op x (Hillis-Steele).
+ *   d_out[i] = x[t0] op x[t0+1] op ... op x[i], t0 = i - i % width.
+ *   op/dt: as cox_tile_reduce.  flags: COX_F_COMPENSATED for F32 SUM (pairs
+ *   (s, e) shuffled together; output fl(s + e)).
+ * Results are reproducible bit for bit (the order above, no fused operations).
+ */
+cox_status cox_tile_scan(cox_op op, cox_dtype dt, int width, int block_dim, const void* d_in,
+                         void* d_out, int64_t n, unsigned flags, void* stream);
+
+/*
+ * cox_ballot_compact -- stable stream compaction driven by warp ballots.
+ *
+ * The filter of the SDK's filter_arr (Table 1) with a static, full-warp group:
+ * b = ballot(key < threshold); rank = popc(b & lanes below); per-block scan of
+ * warp counts; blocks ordered by a single-pass look-back over tile
+ * descriptors.
+ *   dt: COX_I32 (signed compare) or COX_U32 (unsigned compare).
+ *   d_out: room for n elements; receives the kept keys in input order.
+ *   d_count: one int64 on the device, receives the number kept.
+ *   d_workspace: at least cox_ballot_compact_workspace(n, block_dim) bytes,
+ *   16-byte aligned; the call zeroes it first (a cudaMemsetAsync on `stream`)
+ *   unless flags has COX_F_WS_READY, in which case the caller guarantees those
+ *   bytes are zero.  Not shared across concurrent calls.
+ *   flags: 0 or COX_F_WS_READY.
+ * Tiles of block_dim * 16 keys are ordered by a ticket counter; each tile's
+ * look-back polls its predecessors' descriptors.  A poll that exceeds the spin
+ * limit (cox_set_spin_limit) gives up: the tile publishes a zero prefix, writes
+ * nothing, and COX_ETIMEOUT is recorded for cox_device_status().  Every write
+ * stays inside d_out[0, n) and d_count.
+ */
+cox_status cox_ballot_compact(cox_dtype dt, int width, int block_dim, const void* d_keys, int64_t n,
+                              int64_t threshold, void* d_out, int64_t* d_count, void* d_workspace,
+                              size_t workspace_bytes, unsigned flags, void* stream);
+
+size_t cox_ballot_compact_workspace(int64_t n, int block_dim);
+
+/*
+ * cox_match_histogram -- histogram built from __match_any_sync peer groups.
+ *
+ * Per tile: peers = match_any(key); the lowest lane of each peer group adds
+ * popc(peers) to a shared-memory bin; blocks merge into d_hist.  Same family
+ * of warp functions as Section 2.2.1.
+ *   dt: COX_I32 or COX_U32 keys.  bins: 1..8192.
+ *   d_hist: `bins` int32 counters, overwritten (zeroed by the call).
+ *   d_ignored: optional int64 (may be NULL): number of keys outside [0, bins),
+ *   overwritten.
+ */
+cox_status cox_match_histogram(cox_dtype dt, int width, int block_dim, const void* d_keys, int64_t n,
+                               int bins, int32_t* d_hist, int64_t* d_ignored, void* stream);
+
+/*
+ * cox_device_status -- synchronises `stream`, then reads and clears the
+ * device-side status word of the current device.  Returns COX_ETIMEOUT if
+ * any kernel since the last call gave up a bounded wait, COX_ECUDA if the
+ * synchronisation failed, COX_OK otherwise.
+ */
+cox_status cox_device_status(void* stream);
+
+/*
+ * cox_set_spin_limit -- iteration cap of every bounded device-side wait
+ * (look-back, work queues), taken by kernels launched after the call.
+ * 0 restores the default (2^22 polls with back-off, about a second).
+ */
+void cox_set_spin_limit(uint32_t polls);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COX_H_ */

@@ -1,0 +1,242 @@
+"""Python binding of libcox.so (the C ABI declared in include/cox.h).
+
+Argument marshalling only: every step of every op runs in the library's CUDA
+kernels.  ``cox_*`` functions mirror the C entry points one for one (plain
+ints for pointers and the stream) and return the status code; the lower-case
+helpers take torch CUDA tensors, allocate outputs with torch, pass
+``data_ptr()`` and torch's current stream, and raise ``CoxError`` on a
+non-OK status.  There is no fallback: if libcox.so is missing the import of
+the library fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import lib_path
+
+# ------------------------------------------------------------------ codes
+COX_OK, COX_EINVAL, COX_EUNSUPPORTED, COX_ECUDA, COX_ENOMEM, COX_ETIMEOUT, COX_EBUSY = range(7)
+COX_I32, COX_U32, COX_F32 = 0, 1, 2
+COX_SUM, COX_MIN, COX_MAX, COX_AND, COX_OR, COX_XOR = range(6)
+(COX_SHFL_IDX, COX_SHFL_UP, COX_SHFL_DOWN, COX_SHFL_XOR,
+ COX_BALLOT, COX_ANY, COX_ALL, COX_MATCH_ANY) = range(8)
+COX_SCOPE_TILE, COX_SCOPE_BLOCK, COX_SCOPE_GRID = 0, 1, 2
+COX_F_COMPENSATED, COX_F_FP64_COMBINE, COX_F_WS_READY = 1, 2, 4
+FULL_MASK = 0xFFFFFFFF
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_U = ctypes.c_uint
+_SZ = ctypes.c_size_t
+
+# name -> (restype, argtypes), in the order of include/cox.h
+SIGNATURES = {
+    "cox_status_string": (ctypes.c_char_p, [_I]),
+    "cox_version": (_I, []),
+    "cox_shfl": (_I, [_I, _I, _I, _I, _P, _P, _I64, _I, ctypes.c_uint32, _P]),
+    "cox_tile_reduce": (_I, [_I, _I, _I, _I, _I, _P, _P, _I64, _U, _P, _P, _SZ, _P]),
+    "cox_tile_reduce_workspace": (_SZ, [_I, _I64, _I]),
+    "cox_tile_scan": (_I, [_I, _I, _I, _I, _P, _P, _I64, _U, _P]),
+    "cox_ballot_compact": (_I, [_I, _I, _I, _P, _I64, _I64, _P, _P, _P, _SZ, _U, _P]),
+    "cox_ballot_compact_workspace": (_SZ, [_I64, _I]),
+    "cox_match_histogram": (_I, [_I, _I, _I, _P, _I64, _I, _P, _P, _P]),
+    "cox_device_status": (_I, [_P]),
+    "cox_set_spin_limit": (None, [ctypes.c_uint32]),
+}
+
+_lib = None
+
+
+class CoxError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"{what}: {status_string(status)}" if what else status_string(status))
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libcox.so (raises ImportError if it was never built)."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise ImportError(f"libcox.so is not built ({path}); run __graft_entry__.build()")
+        handle = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(handle, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return lib().cox_status_string(int(s)).decode()
+
+
+# ------------------------------------------------------- raw C-ABI mirrors
+def cox_version() -> int:
+    return lib().cox_version()
+
+
+def cox_shfl(fn, dt, width, block_dim, d_in, d_out, n, param, mask, stream) -> int:
+    return lib().cox_shfl(fn, dt, width, block_dim, d_in, d_out, n, param, mask, stream)
+
+
+def cox_tile_reduce(op, dt, width, block_dim, scope, d_in, d_out, n, flags, d_err, d_ws, ws_bytes, stream) -> int:
+    return lib().cox_tile_reduce(op, dt, width, block_dim, scope, d_in, d_out, n, flags, d_err, d_ws, ws_bytes,
+                                 stream)
+
+
+def cox_tile_reduce_workspace(scope, n, block_dim) -> int:
+    return lib().cox_tile_reduce_workspace(scope, n, block_dim)
+
+
+def cox_tile_scan(op, dt, width, block_dim, d_in, d_out, n, flags, stream) -> int:
+    return lib().cox_tile_scan(op, dt, width, block_dim, d_in, d_out, n, flags, stream)
+
+
+def cox_ballot_compact(dt, width, block_dim, d_keys, n, threshold, d_out, d_count, d_ws, ws_bytes, flags,
+                       stream) -> int:
+    return lib().cox_ballot_compact(dt, width, block_dim, d_keys, n, threshold, d_out, d_count, d_ws, ws_bytes,
+                                    flags, stream)
+
+
+def cox_ballot_compact_workspace(n, block_dim) -> int:
+    return lib().cox_ballot_compact_workspace(n, block_dim)
+
+
+def cox_match_histogram(dt, width, block_dim, d_keys, n, bins, d_hist, d_ignored, stream) -> int:
+    return lib().cox_match_histogram(dt, width, block_dim, d_keys, n, bins, d_hist, d_ignored, stream)
+
+
+def cox_device_status(stream) -> int:
+    return lib().cox_device_status(stream)
+
+
+def cox_set_spin_limit(polls: int) -> None:
+    lib().cox_set_spin_limit(polls)
+
+
+# ------------------------------------------------------------ tensor helpers
+def _torch():
+    import torch
+    return torch
+
+
+def _check(status: int, what: str):
+    if status != COX_OK:
+        raise CoxError(status, what)
+
+
+def _stream(dev):
+    return _torch().cuda.current_stream(dev).cuda_stream
+
+
+def _dtype_code(x, unsigned: bool = False) -> int:
+    t = _torch()
+    if x.dtype == t.float32:
+        return COX_F32
+    if x.dtype == t.int32:
+        return COX_U32 if unsigned else COX_I32
+    if hasattr(t, "uint32") and x.dtype == t.uint32:
+        return COX_U32
+    raise TypeError(f"32-bit int or float tensor required, got {x.dtype}")
+
+
+def _dev_tensor(x):
+    if not x.is_cuda:
+        raise ValueError("CUDA tensor required")
+    if not x.is_contiguous():
+        raise ValueError("contiguous tensor required")
+    return x
+
+
+def shfl(fn: int, x, width: int = 32, block_dim: int = 256, param: int = 0, unsigned: bool = False, out=None):
+    """One warp function per lane (cox_shfl).  Masks come back as int32 bit patterns."""
+    t = _torch()
+    x = _dev_tensor(x)
+    dt = _dtype_code(x, unsigned)
+    if out is None:
+        out = t.empty_like(x) if fn <= COX_SHFL_XOR else t.empty(x.shape, dtype=t.int32, device=x.device)
+    _check(cox_shfl(fn, dt, width, block_dim, x.data_ptr(), out.data_ptr(), x.numel(), param, FULL_MASK,
+                    _stream(x.device)), "cox_shfl")
+    return out
+
+
+def reduce_out_len(scope: int, n: int, width: int, block_dim: int) -> int:
+    if scope == COX_SCOPE_TILE:
+        return -(-n // width)
+    if scope == COX_SCOPE_BLOCK:
+        return -(-n // block_dim)
+    return 1
+
+
+def tile_reduce(x, op: int = COX_SUM, width: int = 32, block_dim: int = 256, scope: int = COX_SCOPE_BLOCK,
+                compensated: bool = False, fp64_combine: bool = False, unsigned: bool = False, with_lo: bool = False,
+                workspace=None, out=None):
+    """Tile/block/grid reduction (cox_tile_reduce).  Returns out, or (out, lo) with with_lo."""
+    t = _torch()
+    x = _dev_tensor(x)
+    n = x.numel()
+    m = reduce_out_len(scope, n, width, block_dim)
+    if out is None:
+        out = t.empty(m, dtype=x.dtype, device=x.device)
+    lo = t.zeros(m, dtype=t.float32, device=x.device) if with_lo else None
+    flags = (COX_F_COMPENSATED if compensated else 0) | (COX_F_FP64_COMBINE if fp64_combine else 0)
+    ws_bytes = cox_tile_reduce_workspace(scope, n, block_dim)
+    if ws_bytes and workspace is None:
+        workspace = t.empty(ws_bytes, dtype=t.uint8, device=x.device)
+    _check(cox_tile_reduce(op, _dtype_code(x, unsigned), width, block_dim, scope, x.data_ptr(), out.data_ptr(), n,
+                           flags, lo.data_ptr() if lo is not None else None,
+                           workspace.data_ptr() if workspace is not None else None, ws_bytes,
+                           _stream(x.device)), "cox_tile_reduce")
+    return (out, lo) if with_lo else out
+
+
+def tile_scan(x, op: int = COX_SUM, width: int = 32, block_dim: int = 256, compensated: bool = False,
+              unsigned: bool = False, out=None):
+    """Tile inclusive scan (cox_tile_scan)."""
+    t = _torch()
+    x = _dev_tensor(x)
+    if out is None:
+        out = t.empty_like(x)
+    _check(cox_tile_scan(op, _dtype_code(x, unsigned), width, block_dim, x.data_ptr(), out.data_ptr(), x.numel(),
+                         COX_F_COMPENSATED if compensated else 0, _stream(x.device)), "cox_tile_scan")
+    return out
+
+
+def ballot_compact(keys, threshold: int, width: int = 32, block_dim: int = 256, unsigned: bool = False,
+                   workspace=None, out=None, count=None):
+    """Stable compaction of keys < threshold (cox_ballot_compact).  Returns (out, count) device tensors."""
+    t = _torch()
+    keys = _dev_tensor(keys)
+    n = keys.numel()
+    if out is None:
+        out = t.empty(max(n, 1), dtype=keys.dtype, device=keys.device)
+    if count is None:
+        count = t.empty(1, dtype=t.int64, device=keys.device)
+    ws_bytes = cox_ballot_compact_workspace(n, block_dim)
+    if workspace is None:
+        workspace = t.empty(max(ws_bytes, 16), dtype=t.uint8, device=keys.device)
+    _check(cox_ballot_compact(COX_U32 if unsigned else COX_I32, width, block_dim, keys.data_ptr(), n, int(threshold),
+                              out.data_ptr(), count.data_ptr(), workspace.data_ptr(), workspace.numel(), 0,
+                              _stream(keys.device)), "cox_ballot_compact")
+    return out, count
+
+
+def match_histogram(keys, bins: int = 256, width: int = 32, block_dim: int = 256, unsigned: bool = False):
+    """Match-any histogram (cox_match_histogram).  Returns (hist int32[bins], ignored int64[1])."""
+    t = _torch()
+    keys = _dev_tensor(keys)
+    hist = t.empty(bins, dtype=t.int32, device=keys.device)
+    ign = t.empty(1, dtype=t.int64, device=keys.device)
+    _check(cox_match_histogram(COX_U32 if unsigned else COX_I32, width, block_dim, keys.data_ptr(), keys.numel(),
+                               bins, hist.data_ptr(), ign.data_ptr(), _stream(keys.device)), "cox_match_histogram")
+    return hist, ign
+
+
+def device_status(stream=None) -> int:
+    """Synchronise and read/clear the device status word (cox_device_status)."""
+    return cox_device_status(stream if stream is not None else _stream(None))

@@ -1,0 +1,360 @@
+// Internal helpers shared by the libcox kernels: reducer types, the staging
+// layer that moves warp chunks between HBM and registers, and host dispatch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+#include <utility>
+
+#include "cox.h"
+
+namespace cox {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// ------------------------------------------------------------ device basics
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ uint32_t to_bits(uint32_t v) { return v; }
+__device__ __forceinline__ uint32_t to_bits(int32_t v) { return (uint32_t)v; }
+__device__ __forceinline__ uint32_t to_bits(float v) { return __float_as_uint(v); }
+
+template <class T>
+__device__ __forceinline__ T from_bits(uint32_t u);
+template <>
+__device__ __forceinline__ uint32_t from_bits<uint32_t>(uint32_t u) { return u; }
+template <>
+__device__ __forceinline__ int32_t from_bits<int32_t>(uint32_t u) { return (int32_t)u; }
+template <>
+__device__ __forceinline__ float from_bits<float>(uint32_t u) { return __uint_as_float(u); }
+
+// Knuth's TwoSum: s = fl(a + b), t = (a + b) - s exactly, for any |a|, |b|
+// (Ogita, Rump & Oishi 2005, Alg. 3.1).  The _rn intrinsics are never fused.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+// ----------------------------------------------------------------- reducers
+// A reducer R names the element type T in memory, the register value V, the
+// identity, the combine `op(a, b)`, and how V moves through a shuffle.  For
+// integer ops `redux32` gives the full-warp reduction by redux.sync.
+
+struct AddU {
+  using T = uint32_t;
+  __device__ static T ident() { return 0u; }
+  __device__ static T op(T a, T b) { return a + b; }
+  __device__ static T redux(T v) { return __reduce_add_sync(kFull, v); }
+};
+struct AndU {
+  using T = uint32_t;
+  __device__ static T ident() { return 0xFFFFFFFFu; }
+  __device__ static T op(T a, T b) { return a & b; }
+  __device__ static T redux(T v) { return __reduce_and_sync(kFull, v); }
+};
+struct OrU {
+  using T = uint32_t;
+  __device__ static T ident() { return 0u; }
+  __device__ static T op(T a, T b) { return a | b; }
+  __device__ static T redux(T v) { return __reduce_or_sync(kFull, v); }
+};
+struct XorU {
+  using T = uint32_t;
+  __device__ static T ident() { return 0u; }
+  __device__ static T op(T a, T b) { return a ^ b; }
+  __device__ static T redux(T v) { return __reduce_xor_sync(kFull, v); }
+};
+struct MinI {
+  using T = int32_t;
+  __device__ static T ident() { return 0x7FFFFFFF; }
+  __device__ static T op(T a, T b) { return min(a, b); }
+  __device__ static T redux(T v) { return __reduce_min_sync(kFull, v); }
+};
+struct MaxI {
+  using T = int32_t;
+  __device__ static T ident() { return (int32_t)0x80000000; }
+  __device__ static T op(T a, T b) { return max(a, b); }
+  __device__ static T redux(T v) { return __reduce_max_sync(kFull, v); }
+};
+struct MinU {
+  using T = uint32_t;
+  __device__ static T ident() { return 0xFFFFFFFFu; }
+  __device__ static T op(T a, T b) { return min(a, b); }
+  __device__ static T redux(T v) { return __reduce_min_sync(kFull, v); }
+};
+struct MaxU {
+  using T = uint32_t;
+  __device__ static T ident() { return 0u; }
+  __device__ static T op(T a, T b) { return max(a, b); }
+  __device__ static T redux(T v) { return __reduce_max_sync(kFull, v); }
+};
+struct AddF {
+  using T = float;
+  __device__ static T ident() { return 0.0f; }
+  __device__ static T op(T a, T b) { return __fadd_rn(a, b); }
+};
+struct MinF {
+  using T = float;
+  __device__ static T ident() { return __int_as_float(0x7F800000); }
+  __device__ static T op(T a, T b) { return fminf(a, b); }
+};
+struct MaxF {
+  using T = float;
+  __device__ static T ident() { return __int_as_float(0xFF800000); }
+  __device__ static T op(T a, T b) { return fmaxf(a, b); }
+};
+
+template <class Op>
+struct has_redux {
+  template <class U>
+  static auto test(int) -> decltype(U::redux(typename U::T{}), std::true_type{});
+  template <class>
+  static std::false_type test(...);
+  static constexpr bool value = decltype(test<Op>(0))::value;
+};
+
+// Plain reducer: V == T.
+template <class Op>
+struct Plain {
+  using T = typename Op::T;
+  using V = T;
+  static constexpr bool kComp = false;
+  static constexpr bool kRedux = has_redux<Op>::value;
+  __device__ static V ident() { return Op::ident(); }
+  __device__ static T pad() { return Op::ident(); }  // padding lanes' element
+  __device__ static V load(T x) { return x; }
+  __device__ static V op(V a, V b) { return Op::op(a, b); }
+  __device__ static V shfl_down(V v, int d, int w) { return __shfl_down_sync(kFull, v, d, w); }
+  __device__ static V shfl_up(V v, int d, int w) { return __shfl_up_sync(kFull, v, d, w); }
+  __device__ static V shfl_idx(V v, int s, int w) { return __shfl_sync(kFull, v, s, w); }
+  __device__ static V redux32(V v) {
+    if constexpr (kRedux) return Op::redux(v);
+    else return v;
+  }
+  __device__ static T out(V v) { return v; }
+  __device__ static float lo(V) { return 0.0f; }
+};
+
+// Compensated fp32 sum: a pair (s, e), (s1,e1) (+) (s2,e2) =
+// (s, (e1 + e2) + t) with (s, t) = TwoSum(s1, s2).  Output fl(s + e); the low
+// word `lo` makes out + lo == s + e exactly.
+struct Pair {
+  float s, e;
+};
+struct Comp {
+  using T = float;
+  using V = Pair;
+  static constexpr bool kComp = true;
+  static constexpr bool kRedux = false;
+  __device__ static V ident() { return {0.0f, 0.0f}; }
+  __device__ static T pad() { return 0.0f; }
+  __device__ static V load(T x) { return {x, 0.0f}; }
+  __device__ static V op(V a, V b) {
+    V r;
+    float t;
+    two_sum(a.s, b.s, r.s, t);
+    r.e = __fadd_rn(__fadd_rn(a.e, b.e), t);
+    return r;
+  }
+  __device__ static V shfl_down(V v, int d, int w) {
+    return {__shfl_down_sync(kFull, v.s, d, w), __shfl_down_sync(kFull, v.e, d, w)};
+  }
+  __device__ static V shfl_up(V v, int d, int w) {
+    return {__shfl_up_sync(kFull, v.s, d, w), __shfl_up_sync(kFull, v.e, d, w)};
+  }
+  __device__ static V shfl_idx(V v, int s, int w) {
+    return {__shfl_sync(kFull, v.s, s, w), __shfl_sync(kFull, v.e, s, w)};
+  }
+  __device__ static V redux32(V v) { return v; }
+  __device__ static T out(V v) { return __fadd_rn(v.s, v.e); }
+  __device__ static float lo(V v) {
+    float y, l;
+    two_sum(v.s, v.e, y, l);
+    return l;
+  }
+};
+
+// Width-W shfl_down tree (Code 1 generalised): the tile's rank-0 lane ends
+// with the tile's value.  Integer reducers at W == 32 use redux.sync, which
+// gives every lane the same (exact) value.
+template <class R, int W>
+__device__ __forceinline__ typename R::V tile_tree(typename R::V v) {
+  if constexpr (W == 32 && R::kRedux) {
+    return R::redux32(v);
+  } else {
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1) v = R::op(v, R::shfl_down(v, off, W));
+    return v;
+  }
+}
+
+// ------------------------------------------------------------ staging layer
+// A warp chunk is ROWS rows of 32 consecutive 32-bit elements; after loading,
+// lane l holds row[r] = element base + 32 r + l (the paper's lane numbering:
+// element i is the operand of global thread i).  Full chunks move as 128-bit
+// (ROWS >= 4), 64-bit (ROWS == 2) or 32-bit (ROWS == 1) coalesced accesses
+// and are transposed through a warp-private shared-memory buffer of ROWS*32
+// words; partial chunks use 32-bit accesses with padding.
+
+template <int ROWS>
+__device__ __forceinline__ void load_rows_full(const uint32_t* __restrict__ g, uint32_t* sm,
+                                               uint32_t (&row)[ROWS]) {
+  const int lane = lane_id();
+  if constexpr (ROWS >= 4) {
+    constexpr int NV = ROWS / 4;
+    uint4 v[NV];
+    const uint4* src = reinterpret_cast<const uint4*>(g);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = __ldcs(src + j * 32 + lane);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) reinterpret_cast<uint4*>(sm)[j * 32 + lane] = v[j];
+  } else if constexpr (ROWS == 2) {
+    const uint2 v = __ldcs(reinterpret_cast<const uint2*>(g) + lane);
+    reinterpret_cast<uint2*>(sm)[lane] = v;
+  } else {
+    row[0] = __ldcs(g + lane);
+    return;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) row[r] = sm[r * 32 + lane];
+  __syncwarp();
+}
+
+template <int ROWS>
+__device__ __forceinline__ void load_rows_tail(const uint32_t* __restrict__ g, int64_t avail,
+                                               uint32_t pad, uint32_t (&row)[ROWS]) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    const int64_t i = (int64_t)r * 32 + lane;
+    row[r] = i < avail ? g[i] : pad;
+  }
+}
+
+template <int ROWS>
+__device__ __forceinline__ void store_rows_full(uint32_t* __restrict__ g, uint32_t* sm,
+                                                const uint32_t (&row)[ROWS]) {
+  const int lane = lane_id();
+  if constexpr (ROWS == 1) {
+    __stcs(g + lane, row[0]);
+    return;
+  } else {
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) sm[r * 32 + lane] = row[r];
+    __syncwarp();
+    if constexpr (ROWS >= 4) {
+#pragma unroll
+      for (int j = 0; j < ROWS / 4; ++j)
+        __stcs(reinterpret_cast<uint4*>(g) + j * 32 + lane, reinterpret_cast<const uint4*>(sm)[j * 32 + lane]);
+    } else {
+      __stcs(reinterpret_cast<uint2*>(g) + lane, reinterpret_cast<const uint2*>(sm)[lane]);
+    }
+    __syncwarp();
+  }
+}
+
+template <int ROWS>
+__device__ __forceinline__ void store_rows_tail(uint32_t* __restrict__ g, int64_t avail,
+                                                const uint32_t (&row)[ROWS]) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    const int64_t i = (int64_t)r * 32 + lane;
+    if (i < avail) g[i] = row[r];
+  }
+}
+
+// ------------------------------------------------- device status + waits
+// Bit flags of the device-side status word read by cox_device_status().
+enum : unsigned { kDevTimeout = 1u };
+
+// Defined in api.cu (relocatable device code is not used: each kernel file
+// reaches the word through this accessor, which api.cu implements).
+__host__ unsigned* device_status_word();
+__host__ uint32_t spin_limit();
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// ------------------------------------------------------------ host helpers
+inline bool valid_width(int w) { return w == 2 || w == 4 || w == 8 || w == 16 || w == 32; }
+inline bool valid_block(int b) { return b >= 32 && b <= 1024 && b % 32 == 0; }
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int sm_count();  // of the current device (cached per device)
+
+inline cox_status launch_status() {
+  return cudaGetLastError() == cudaSuccess ? COX_OK : COX_ECUDA;
+}
+
+// Calls f(Reducer{}) for the reducer of (op, dt, compensated).
+template <class F>
+cox_status with_reducer(cox_op op, cox_dtype dt, bool comp, F&& f) {
+  if (comp) {
+    if (dt != COX_F32 || op != COX_SUM) return COX_EINVAL;
+    return f(Comp{});
+  }
+  if (dt == COX_F32) {
+    switch (op) {
+      case COX_SUM: return f(Plain<AddF>{});
+      case COX_MIN: return f(Plain<MinF>{});
+      case COX_MAX: return f(Plain<MaxF>{});
+      default: return COX_EINVAL;
+    }
+  }
+  if (dt != COX_I32 && dt != COX_U32) return COX_EINVAL;
+  switch (op) {
+    case COX_SUM: return f(Plain<AddU>{});
+    case COX_AND: return f(Plain<AndU>{});
+    case COX_OR: return f(Plain<OrU>{});
+    case COX_XOR: return f(Plain<XorU>{});
+    case COX_MIN: return dt == COX_I32 ? f(Plain<MinI>{}) : f(Plain<MinU>{});
+    case COX_MAX: return dt == COX_I32 ? f(Plain<MaxI>{}) : f(Plain<MaxU>{});
+    default: return COX_EINVAL;
+  }
+}
+
+template <class F>
+cox_status with_width(int w, F&& f) {
+  switch (w) {
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    case 8: return f(std::integral_constant<int, 8>{});
+    case 16: return f(std::integral_constant<int, 16>{});
+    case 32: return f(std::integral_constant<int, 32>{});
+    default: return COX_EINVAL;
+  }
+}
+
+// Persistent-grid size for a kernel: resident CTAs per SM (occupancy query,
+// cached by the caller) x SMs, capped by the work available.
+template <class K>
+int persistent_grid(K kernel, int block, size_t dyn_smem, int64_t work_ctas) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, dyn_smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  int64_t g = (int64_t)per_sm * sm_count();
+  if (work_ctas < g) g = work_ctas;
+  return g < 1 ? 1 : (int)g;
+}
+
+}  // namespace cox

@@ -1,0 +1,123 @@
+// cox_match_histogram: histogram from __match_any_sync peer groups.
+//
+// Per warp step every lane holds one key; peers = match_any(key) restricted to
+// the lane's width-W tile and to lanes that hold a key; the lowest peer (the
+// group's leader) adds popc(peers) to a shared-memory bin, so equal keys in a
+// tile cost one shared atomic instead of one each.  Keys outside [0, bins)
+// are counted as ignored.  Shared histograms are per warp when they fit (no
+// cross-warp contention on hot bins, e.g. Zipf keys), else per CTA; each CTA
+// merges its non-zero bins into the output with global atomics.  Integer
+// counts: the result does not depend on which lanes group together.
+#include "cox_common.cuh"
+
+namespace cox {
+
+template <int W>
+__device__ __forceinline__ void hist_step(uint32_t key, bool valid, uint32_t bins, uint32_t* my,
+                                          uint32_t& ign) {
+  const int lane = lane_id();
+  const unsigned tmask = W == 32 ? kFull : (((1u << W) - 1u) << (lane & ~(W - 1)));
+  const unsigned vb = __ballot_sync(kFull, valid);
+  const unsigned peers = __match_any_sync(kFull, key) & vb & tmask;
+  if (valid && (peers & lanemask_lt()) == 0u) {
+    const uint32_t c = __popc(peers);
+    if (key < bins) atomicAdd(my + key, c);
+    else ign += c;
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(1024) k_match_hist(const uint32_t* __restrict__ keys, int64_t n, uint32_t bins,
+                                                     int per_warp, int32_t* __restrict__ hist,
+                                                     unsigned long long* ignored, int vec) {
+  extern __shared__ uint32_t sh[];
+  __shared__ uint32_t s_ign;
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = lane_id();
+  const int nsh = per_warp ? nw * (int)bins : (int)bins;
+  for (int i = threadIdx.x; i < nsh; i += blockDim.x) sh[i] = 0u;
+  if (threadIdx.x == 0) s_ign = 0u;
+  __syncthreads();
+  uint32_t* my = per_warp ? sh + warp * bins : sh;
+  uint32_t ign = 0;
+  // Each warp step covers 128 consecutive keys (one 128-bit load per lane).
+  const int64_t nsteps = (n + 127) / 128;
+  const int64_t gw = (int64_t)blockIdx.x * nw + warp, gws = (int64_t)gridDim.x * nw;
+  int64_t s = gw;
+  if (vec) {
+    for (; s + gws < nsteps && (s + gws + 1) * 128 <= n; s += 2 * gws) {  // two loads in flight
+      const uint4 a = __ldcs(reinterpret_cast<const uint4*>(keys + s * 128) + lane);
+      const uint4 b = __ldcs(reinterpret_cast<const uint4*>(keys + (s + gws) * 128) + lane);
+      hist_step<W>(a.x, true, bins, my, ign);
+      hist_step<W>(a.y, true, bins, my, ign);
+      hist_step<W>(a.z, true, bins, my, ign);
+      hist_step<W>(a.w, true, bins, my, ign);
+      hist_step<W>(b.x, true, bins, my, ign);
+      hist_step<W>(b.y, true, bins, my, ign);
+      hist_step<W>(b.z, true, bins, my, ign);
+      hist_step<W>(b.w, true, bins, my, ign);
+    }
+  }
+  for (; s < nsteps; s += gws) {
+    const int64_t e0 = s * 128 + 4 * lane;
+    uint32_t k[4];
+    bool v[4];
+    if (vec && s * 128 + 128 <= n) {
+      const uint4 a = __ldcs(reinterpret_cast<const uint4*>(keys + s * 128) + lane);
+      k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w;
+      v[0] = v[1] = v[2] = v[3] = true;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        v[q] = e0 + q < n;
+        k[q] = v[q] ? keys[e0 + q] : 0u;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) hist_step<W>(k[q], v[q], bins, my, ign);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) ign += __shfl_xor_sync(kFull, ign, off);
+  if (lane == 0 && ign) atomicAdd(&s_ign, ign);
+  __syncthreads();
+  for (uint32_t b = threadIdx.x; b < bins; b += blockDim.x) {
+    uint32_t c = 0;
+    if (per_warp) {
+      for (int w = 0; w < nw; ++w) c += sh[w * bins + b];
+    } else {
+      c = sh[b];
+    }
+    if (c) atomicAdd(hist + b, (int32_t)c);
+  }
+  if (threadIdx.x == 0 && s_ign && ignored) atomicAdd(ignored, (unsigned long long)s_ign);
+}
+
+}  // namespace cox
+
+using namespace cox;
+
+extern "C" cox_status cox_match_histogram(cox_dtype dt, int width, int block_dim, const void* d_keys, int64_t n,
+                                          int bins, int32_t* d_hist, int64_t* d_ignored, void* stream) {
+  if (!valid_width(width) || !valid_block(block_dim) || n < 0) return COX_EINVAL;
+  if (dt != COX_I32 && dt != COX_U32) return COX_EINVAL;
+  if (bins < 1 || bins > 8192 || !d_hist || (n > 0 && !d_keys)) return COX_EINVAL;
+  cudaStream_t st = as_stream(stream);
+  if (cudaMemsetAsync(d_hist, 0, (size_t)bins * sizeof(int32_t), st) != cudaSuccess) return COX_ECUDA;
+  if (d_ignored && cudaMemsetAsync(d_ignored, 0, sizeof(int64_t), st) != cudaSuccess) return COX_ECUDA;
+  if (n == 0) return COX_OK;
+  const int nw = block_dim / 32;
+  const int per_warp = (size_t)nw * bins * 4 <= 48 * 1024;
+  const size_t smem = (size_t)(per_warp ? nw * bins : bins) * 4;
+  const int vec = aligned16(d_keys);
+  return with_width(width, [&](auto w) {
+    auto k = k_match_hist<decltype(w)::value>;
+    static int gmax[33][49];  // by warps per CTA and shared KiB
+    int& g = gmax[nw][(smem + 1023) / 1024];
+    if (g == 0) g = persistent_grid(k, block_dim, smem, 1 << 30);
+    const int64_t steps = (n + 127) / 128;
+    const int64_t ctas = (steps + nw - 1) / nw;
+    k<<<(int)(ctas < g ? ctas : g), block_dim, smem, st>>>(static_cast<const uint32_t*>(d_keys), n,
+                                                           (uint32_t)bins, per_warp, d_hist,
+                                                           reinterpret_cast<unsigned long long*>(d_ignored), vec);
+    return launch_status();
+  });
+}

@@ -1,0 +1,86 @@
+// cox_tile_scan: inclusive scan inside cooperative-groups tiles of width W.
+//
+// The shuffle scan of the SDK kernel shfl_scan_test (Table 1 of the paper),
+// run on a tile: Hillis-Steele steps d = 1, 2, .., W/2 of
+//   u = shfl_up(x, d, W); if (rank >= d) x = u op x
+// with the lane numbering of Code 3 (element i is global thread i's operand).
+// Persistent warps stream chunks of ROWS x 32 elements: 128-bit loads,
+// a warp-private shared-memory transpose to one element per lane per row,
+// ROWS independent shuffle chains (instruction-level parallelism), and the
+// inverse transpose to 128-bit stores.
+#include "cox_common.cuh"
+
+namespace cox {
+
+constexpr int kScanRows = 8;
+
+template <class R, int W, int ROWS>
+__global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__ in,
+                                                   uint32_t* __restrict__ out, int64_t n, int vec) {
+  using T = typename R::T;
+  using V = typename R::V;
+  extern __shared__ uint32_t smem[];
+  uint32_t* sm = smem + (threadIdx.x >> 5) * (ROWS * 32);
+  constexpr int64_t CH = ROWS * 32;
+  const int64_t nchunks = (n + CH - 1) / CH;
+  const int64_t nfull = vec ? n / CH : 0;
+  const int rank = lane_id() & (W - 1);
+  const int64_t wpb = blockDim.x >> 5;
+  const uint32_t pad = to_bits(R::pad());
+  for (int64_t c = blockIdx.x * wpb + (threadIdx.x >> 5); c < nchunks; c += gridDim.x * wpb) {
+    const int64_t base = c * CH;
+    const bool full = c < nfull;
+    uint32_t row[ROWS];
+    if (full) load_rows_full<ROWS>(in + base, sm, row);
+    else load_rows_tail<ROWS>(in + base, n - base, pad, row);
+    V v[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) v[r] = R::load(from_bits<T>(row[r]));
+#pragma unroll
+    for (int d = 1; d < W; d <<= 1) {
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        const V u = R::shfl_up(v[r], d, W);
+        if (rank >= d) v[r] = R::op(u, v[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) row[r] = to_bits(R::out(v[r]));
+    if (full) store_rows_full<ROWS>(out + base, sm, row);
+    else store_rows_tail<ROWS>(out + base, n - base, row);
+  }
+}
+
+template <class R, int W>
+static cox_status launch_scan(const void* in, void* out, int64_t n, int block, cudaStream_t st) {
+  auto k = k_tile_scan<R, W, kScanRows>;
+  const size_t smem = (size_t)(block / 32) * kScanRows * 32 * 4;
+  const int64_t chunks = (n + kScanRows * 32 - 1) / (kScanRows * 32);
+  const int64_t ctas = (chunks + block / 32 - 1) / (block / 32);
+  static int grid_cache[33];  // persistent grid per block size (occupancy does not change)
+  int& g = grid_cache[block / 32];
+  if (g == 0) g = persistent_grid(k, block, smem, 1 << 30);
+  const int grid = (int)(ctas < g ? ctas : g);
+  const int vec = aligned16(in) && aligned16(out);
+  k<<<grid, block, smem, st>>>(static_cast<const uint32_t*>(in), static_cast<uint32_t*>(out), n, vec);
+  return launch_status();
+}
+
+}  // namespace cox
+
+using namespace cox;
+
+extern "C" cox_status cox_tile_scan(cox_op op, cox_dtype dt, int width, int block_dim, const void* d_in,
+                                    void* d_out, int64_t n, unsigned flags, void* stream) {
+  if (!valid_width(width) || !valid_block(block_dim) || n < 0) return COX_EINVAL;
+  if (flags & ~(unsigned)COX_F_COMPENSATED) return COX_EINVAL;
+  if (n > 0 && (!d_in || !d_out)) return COX_EINVAL;
+  const bool comp = flags & COX_F_COMPENSATED;
+  return with_reducer(op, dt, comp, [&](auto r) {
+    using R = decltype(r);
+    return with_width(width, [&](auto w) {
+      if (n == 0) return COX_OK;
+      return launch_scan<R, decltype(w)::value>(d_in, d_out, n, block_dim, as_stream(stream));
+    });
+  });
+}
