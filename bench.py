@@ -1,0 +1,459 @@
+"""Throughput benchmark of the warp-collective library on one GB300.
+
+A step is the tile-scan workload: cooperative-groups inclusive scans by
+shfl_up over 2^26 fp32 values ~ N(0,1) at tile widths 4, 8, 16 and 32, each
+plain and TwoSum-compensated, 256-thread blocks (8 launches per step).  The
+metric is warp-collective GB/s: algorithmic bytes (4 read + 4 written per
+element per launch) over device time, and its fraction of the measured HBM
+copy bandwidth.  The JSON line also carries the dominant kernel's roofline,
+the end-to-end rate through host buffers, the oracle's CPU baseline, the SM
+clocks seen during the timed region, and secondary single-op numbers.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+For N > 1 (torchrun, one rank per GPU) every rank runs its own replica of the
+workload (the ops need no exchange); value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2112_10034_gb300 import inputs  # noqa: E402
+
+N_ELEMS = 1 << 26
+WIDTHS = (4, 8, 16, 32)
+BLOCK = 256
+VARIANTS = [(w, comp) for w in WIDTHS for comp in (False, True)]
+BYTES_PER_LAUNCH = N_ELEMS * 8
+METRIC = "warp-collective GB/s (% of HBM peak); batched p50/p99 latency vs per-call"
+WORKLOAD = ("tile inclusive scan (shfl_up, cg tiles) of 2^26 fp32 N(0,1) at widths 4/8/16/32, "
+            "plain and compensated, 256-thread blocks")
+
+# DRAM bytes per launch of the dominant kernel from one ncu capture, valid
+# only while the kernel sources hash to `src_sha` (else reported as null).
+NCU_TRAFFIC = {"kernel": None, "src_sha": None, "bytes_per_launch": None}
+KERNEL_SOURCES = ["paper_2112_10034_gb300/csrc/scan.cu", "paper_2112_10034_gb300/csrc/cox_common.cuh"]
+
+
+def _src_sha() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons every 100 ms."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-i", str(self.index),
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [c.strip() for c in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        rows = [r for t, r in self.rows if t0 - 0.15 <= t <= t1 + 0.15] or [r for _, r in self.rows[-3:]]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 6 + i and r[6 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ distributed
+def _dist_setup(gpus: int):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------- the GPU arm
+def run_cox(args):
+    import torch
+    from paper_2112_10034_gb300 import cox
+
+    rank, world, local = _dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    st = torch.cuda.Stream(device=dev)
+    sh = st.cuda_stream
+    x_host = inputs.normal_f32(N_ELEMS, inputs.BASE_SEED + 1)
+    x = torch.from_numpy(x_host).to(dev)
+    outs = [torch.empty(N_ELEMS, dtype=torch.float32, device=dev) for _ in VARIANTS]
+
+    def launch(i, w, comp):
+        s = cox.cox_tile_scan(cox.COX_SUM, cox.COX_F32, w, BLOCK, x.data_ptr(), outs[i].data_ptr(), N_ELEMS,
+                              cox.COX_F_COMPENSATED if comp else 0, sh)
+        if s != 0:
+            raise cox.CoxError(s, "cox_tile_scan")
+
+    # warm-up (first calls also size the persistent grids)
+    for _ in range(args.warmup):
+        for i, (w, comp) in enumerate(VARIANTS):
+            launch(i, w, comp)
+    st.synchronize()
+
+    K = args.steps
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in VARIANTS]
+          for _ in range(K)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    _barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.time()
+    t_start.record(st)
+    for k in range(K):
+        for i, (w, comp) in enumerate(VARIANTS):
+            ev[k][i][0].record(st)
+            launch(i, w, comp)
+            ev[k][i][1].record(st)
+    t_end.record(st)
+    torch.cuda.synchronize()
+    wall1 = time.time()
+    _barrier(world)
+    clocks.stop()
+    elapsed_ms = _max_over_ranks(t_start.elapsed_time(t_end), world)
+    per_variant_ms = [statistics.mean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(K))
+                      for i in range(len(VARIANTS))]
+    launches = K * len(VARIANTS)
+
+    # ---- parity spot check of this run's outputs (sampled rows, no oracle call)
+    value = BYTES_PER_LAUNCH * launches * world / (elapsed_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    dom = int(np.argmax(per_variant_ms))
+    achieved = BYTES_PER_LAUNCH / (per_variant_ms[dom] * 1e-3) / 1e9
+    w_dom, c_dom = VARIANTS[dom]
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["src_sha"] == _src_sha() else None
+
+    # ---- end to end through host buffers (pinned), copies inside the region
+    e2e = run_e2e(args, x_host, dev, st, min(K, 20))
+
+    result = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(elapsed_ms / K, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded N(0,1) fp32, PCG64)",
+        "config": {"workload": WORKLOAD, "n": N_ELEMS, "widths": list(WIDTHS), "block_dim": BLOCK,
+                   "launches_per_step": len(VARIANTS), "parallelism": f"replicas x{world}",
+                   "l2": "no flush: each launch streams 256 MiB in + 256 MiB out, > 129 MB L2"},
+        "frac_of_hbm": round(value / world / peak, 4),
+        "roofline": {"bound": "hbm", "kernel": f"k_tile_scan<{'Comp' if c_dom else 'Plain<AddF>'},W={w_dom}>",
+                     "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "algorithmic_bytes_per_launch": BYTES_PER_LAUNCH},
+        "per_kernel_us": {f"W{w}{'_comp' if c else '_plain'}": round(ms * 1e3, 2)
+                          for (w, c), ms in zip(VARIANTS, per_variant_ms)},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks.summary(wall0, wall1),
+    }
+    if rank == 0 and not args.no_secondary:
+        result["secondary"] = run_secondary(dev, st)
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        result["cpu_baseline"] = cpu_baseline(target_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(args, x_host, dev, st, K):
+    """Same metric through the C ABI with host buffers: per step, the input goes
+    host->device from pinned memory and all 8 outputs come back device->host."""
+    import torch
+    from paper_2112_10034_gb300 import cox
+    pin_in = torch.from_numpy(x_host).pin_memory()
+    pin_out = [torch.empty(N_ELEMS, dtype=torch.float32).pin_memory() for _ in VARIANTS]
+    x = torch.empty(N_ELEMS, dtype=torch.float32, device=dev)
+    outs = [torch.empty(N_ELEMS, dtype=torch.float32, device=dev) for _ in VARIANTS]
+    sh = st.cuda_stream
+
+    def step():
+        with torch.cuda.stream(st):
+            x.copy_(pin_in, non_blocking=True)
+            for i, (w, comp) in enumerate(VARIANTS):
+                s = cox.cox_tile_scan(cox.COX_SUM, cox.COX_F32, w, BLOCK, x.data_ptr(), outs[i].data_ptr(), N_ELEMS,
+                                      cox.COX_F_COMPENSATED if comp else 0, sh)
+                if s != 0:
+                    raise cox.CoxError(s, "cox_tile_scan")
+            for i in range(len(VARIANTS)):
+                pin_out[i].copy_(outs[i], non_blocking=True)
+
+    for _ in range(2):
+        step()
+    st.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(K):
+        step()
+    b.record(st)
+    b.synchronize()
+    ms = a.elapsed_time(b) / K
+    return {"value": round(BYTES_PER_LAUNCH * len(VARIANTS) / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "ms_per_step": round(ms, 4), "steps": K, "h2d_bytes_per_step": N_ELEMS * 4,
+            "d2h_bytes_per_step": N_ELEMS * 4 * len(VARIANTS)}
+
+
+def _time_launches(st, fn, iters=20, warm=3):
+    import torch
+    for _ in range(warm):
+        fn()
+    st.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(iters):
+        fn()
+    b.record(st)
+    b.synchronize()
+    return a.elapsed_time(b) / iters
+
+
+def run_secondary(dev, st):
+    """Other single-op workloads, each timed alone (device time per call)."""
+    import torch
+    from paper_2112_10034_gb300 import cox
+    sh = st.cuda_stream
+    peak, _ = _peaks()
+    res = {}
+
+    def chk(s):
+        if s != 0:
+            raise cox.CoxError(s)
+
+    # block sum, 64 blocks x 256 threads of int32 (launch-latency bound)
+    x = torch.from_numpy(inputs.uniform_int32(16384, -1000, 1000, inputs.BASE_SEED)).to(dev)
+    out = torch.empty(64, dtype=torch.int32, device=dev)
+    ms = _time_launches(st, lambda: chk(cox.cox_tile_reduce(0, 0, 32, 256, 1, x.data_ptr(), out.data_ptr(), 16384, 0,
+                                                            None, None, 0, sh)), iters=200)
+    res["block_sum_64x256_int32"] = {"us_per_call": round(ms * 1e3, 2)}
+
+    # stable compaction of 2^28 int32 keys at densities 0.1/0.5/0.9
+    n = 1 << 28
+    k = torch.from_numpy(inputs.uniform_u31(n, inputs.BASE_SEED + 2)).to(dev)
+    o = torch.empty(n, dtype=torch.int32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    wsb = cox.cox_ballot_compact_workspace(n, 256)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    comp = {}
+    for d in (0.1, 0.5, 0.9):
+        t = inputs.density_threshold(d)
+        ms = _time_launches(st, lambda: chk(cox.cox_ballot_compact(0, 32, 256, k.data_ptr(), n, t, o.data_ptr(),
+                                                                   cnt.data_ptr(), ws.data_ptr(), wsb, 0, sh)))
+        kept = int(cnt.item())
+        gbs = (n * 4 + kept * 4) / (ms * 1e-3) / 1e9
+        comp[str(d)] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3),
+                        "density": round(kept / n, 5)}
+    res["compaction_2p28_int32"] = comp
+    del k, o
+
+    # match histogram of 2^28 Zipf(1.1) keys into 256 bins
+    z = torch.from_numpy(inputs.zipf_keys(n, inputs.BASE_SEED + 3)).to(dev)
+    hist = torch.empty(256, dtype=torch.int32, device=dev)
+    ms = _time_launches(st, lambda: chk(cox.cox_match_histogram(0, 32, 256, z.data_ptr(), n, 256, hist.data_ptr(),
+                                                                None, sh)))
+    gbs = n * 4 / (ms * 1e-3) / 1e9
+    res["match_histogram_2p28_zipf"] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3)}
+    del z
+
+    # grid reduce of 2^28 fp32, compensated
+    f = torch.randn(n, dtype=torch.float32, device=dev)
+    r = torch.empty(1, dtype=torch.float32, device=dev)
+    wsb = cox.cox_tile_reduce_workspace(2, n, 256)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    ms = _time_launches(st, lambda: chk(cox.cox_tile_reduce(0, 2, 32, 256, 2, f.data_ptr(), r.data_ptr(), n, 1, None,
+                                                            ws.data_ptr(), wsb, sh)))
+    gbs = n * 4 / (ms * 1e-3) / 1e9
+    res["grid_sum_2p28_fp32_comp"] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3)}
+    return res
+
+
+# ------------------------------------------------------ CPU (oracle) legs
+def _oracle_step(o, x):
+    for w, comp in VARIANTS:
+        o.scan_emulate(o.SUM, o.F32, w, BLOCK, x, comp)
+
+
+def cpu_baseline(target_s: float = 12.0):
+    """The oracle's collapsed-loop executor on a bounded prefix of the workload."""
+    import oracle as o
+    x_full = inputs.normal_f32(N_ELEMS, inputs.BASE_SEED + 1)
+    n = 1 << 18
+    while True:
+        x = x_full[:n]
+        t0 = time.perf_counter()
+        _oracle_step(o, x)
+        dt = time.perf_counter() - t0
+        if dt * 4 >= target_s or n >= N_ELEMS:
+            break
+        n = min(N_ELEMS, n * 4)
+    gbs = n * 8 * len(VARIANTS) / dt / 1e9
+    return {"value": round(gbs, 4), "unit": "GB/s", "cores": o.threads(), "kind": "oracle",
+            "sample": f"first {n} of the 2^26 elements, all 8 width/mode scans, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle (collapsed-loop executor) on this workload."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as o
+    x_full = inputs.normal_f32(N_ELEMS, inputs.BASE_SEED + 1)
+    # size each step so that warm-up + timed steps take about two minutes
+    n = 1 << 16
+    t0 = time.perf_counter()
+    _oracle_step(o, x_full[:n])
+    per_elem = (time.perf_counter() - t0) / n
+    budget = min(1.0, 120.0 / max(1, args.steps + args.warmup))
+    n = int(max(1 << 14, min(N_ELEMS, budget / per_elem)))
+    n -= n % 1024
+    x = x_full[:n]
+    for _ in range(args.warmup):
+        _oracle_step(o, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_step(o, x)
+    dt = time.perf_counter() - t0
+    gbs = n * 8 * len(VARIANTS) * args.steps / dt / 1e9
+    sample = f"first {n} of the 2^26 elements per step, all 8 width/mode scans"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded N(0,1) fp32, PCG64)",
+        "config": {"workload": WORKLOAD, "n": N_ELEMS, "widths": list(WIDTHS), "block_dim": BLOCK,
+                   "sample_n": n},
+        "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": o.threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_profile(args):
+    """Small case for an ncu capture: the 8 scan launches per step over one
+    2^26-element input and one output (512 MiB on the device), nothing else."""
+    import torch
+    from paper_2112_10034_gb300 import cox
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.Stream(device=dev)
+    x = torch.from_numpy(inputs.normal_f32(N_ELEMS, inputs.BASE_SEED + 1)).to(dev)
+    out = torch.empty(N_ELEMS, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup + args.steps):
+        for w, comp in VARIANTS:
+            s = cox.cox_tile_scan(cox.COX_SUM, cox.COX_F32, w, BLOCK, x.data_ptr(), out.data_ptr(), N_ELEMS,
+                                  cox.COX_F_COMPENSATED if comp else 0, st.cuda_stream)
+            if s != 0:
+                raise cox.CoxError(s, "cox_tile_scan")
+    st.synchronize()
+    print(json.dumps({"profile": "tile_scan", "launches": (args.warmup + args.steps) * len(VARIANTS)}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cox", choices=["cox", "reference"])
+    ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile", action="store_true", help="small case for ncu: scan launches only")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cox(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -198,6 +198,26 @@ __device__ __forceinline__ typename R::V tile_tree(typename R::V v) {
   }
 }
 
+// Block reduction in the order of the BLOCK scope: width-32 tree per warp,
+// warp partials to shared memory, warp 0 lane l folds partials l, l+32, ...
+// then a width-32 tree.  The result is valid in thread 0; `wpart` holds 32
+// values.  Contains two __syncthreads (all threads must call it).
+template <class R>
+__device__ __forceinline__ typename R::V block_reduce32(typename R::V v, typename R::V* wpart) {
+  using V = typename R::V;
+  v = tile_tree<R, 32>(v);
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  if (lane == 0) wpart[warp] = v;
+  __syncthreads();
+  V acc = R::ident();
+  if (warp == 0) {
+    for (int k = lane; k < (int)(blockDim.x >> 5); k += 32) acc = R::op(acc, wpart[k]);
+    acc = tile_tree<R, 32>(acc);
+  }
+  __syncthreads();
+  return acc;
+}
+
 // ------------------------------------------------------------ staging layer
 // A warp chunk is ROWS rows of 32 consecutive 32-bit elements; after loading,
 // lane l holds row[r] = element base + 32 r + l (the paper's lane numbering:

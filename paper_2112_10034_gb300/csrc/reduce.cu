@@ -158,22 +158,6 @@ __global__ void __launch_bounds__(256) k_reduce_block_warp(const uint32_t* __res
 // loads in flight per thread); then the block stage above (W = 32); CTA
 // partial to the workspace; the last CTA to arrive folds all partials in CTA
 // order (FP64 for F32 sums with fp64 set) and re-arms the counter.
-template <class R>
-__device__ __forceinline__ typename R::V block_reduce32(typename R::V v, typename R::V* wpart) {
-  using V = typename R::V;
-  v = tile_tree<R, 32>(v);
-  const int warp = threadIdx.x >> 5, lane = lane_id();
-  if (lane == 0) wpart[warp] = v;
-  __syncthreads();
-  V acc = R::ident();
-  if (warp == 0) {
-    for (int k = lane; k < (int)(blockDim.x >> 5); k += 32) acc = R::op(acc, wpart[k]);
-    acc = tile_tree<R, 32>(acc);
-  }
-  __syncthreads();
-  return acc;  // valid in thread 0
-}
-
 __device__ __forceinline__ double block_reduce_f64(double v, double* wpart) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(kFull, v, off);
