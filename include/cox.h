@@ -176,6 +176,33 @@ cox_status cox_ballot_compact(cox_dtype dt, int width, int block_dim, const void
 size_t cox_ballot_compact_workspace(int64_t n, int block_dim);
 
 /*
+ * cox_ballot_compact_static -- cox_ballot_compact without a workspace, for
+ * callers that cannot allocate device memory: code running under a host
+ * framework whose allocator owns the whole device budget and forbids side
+ * allocations, or a latency-critical loop that must not take the implicit
+ * device synchronisation of cudaMalloc/cudaFree, or a plugin that is handed
+ * only its input and output buffers.  The paper has no counterpart; this is
+ * a library convenience.
+ *
+ * Same arguments and results as cox_ballot_compact minus the workspace and
+ * flags.  The scratch is a fixed array of COX_COMPACT_STATIC_SCRATCH_BYTES
+ * (1 MiB) inside libcox.so, held on every GPU that loads the library until
+ * the process exits.  It fits 256 bytes of header plus 8 bytes per tile of
+ * block_dim * 16 keys: n <= 131040 * block_dim * 16 (536,739,840 keys at
+ * block_dim 256).  Larger n returns COX_ENOMEM before anything is enqueued.
+ * The call allocates nothing (no cudaMalloc/cudaFree) and clears the scratch
+ * bytes it uses with a cudaMemsetAsync on `stream` before its kernel.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture on the device.  All calls share the one array: calls whose work
+ * overlaps on the GPU (other streams, other threads) race on it and must be
+ * serialised by the caller.
+ */
+#define COX_COMPACT_STATIC_SCRATCH_BYTES (1u << 20)
+cox_status cox_ballot_compact_static(cox_dtype dt, int width, int block_dim, const void* d_keys, int64_t n,
+                                     int64_t threshold, void* d_out, int64_t* d_count, void* stream);
+
+/*
  * cox_match_histogram -- histogram built from __match_any_sync peer groups.
  *
  * Per tile: peers = match_any(key); the lowest lane of each peer group adds

@@ -41,6 +41,7 @@ SIGNATURES = {
     "cox_tile_scan": (_I, [_I, _I, _I, _I, _P, _P, _I64, _U, _P]),
     "cox_ballot_compact": (_I, [_I, _I, _I, _P, _I64, _I64, _P, _P, _P, _SZ, _U, _P]),
     "cox_ballot_compact_workspace": (_SZ, [_I64, _I]),
+    "cox_ballot_compact_static": (_I, [_I, _I, _I, _P, _I64, _I64, _P, _P, _P]),
     "cox_match_histogram": (_I, [_I, _I, _I, _P, _I64, _I, _P, _P, _P]),
     "cox_device_status": (_I, [_P]),
     "cox_set_spin_limit": (None, [ctypes.c_uint32]),
@@ -105,6 +106,13 @@ def cox_ballot_compact(dt, width, block_dim, d_keys, n, threshold, d_out, d_coun
 
 def cox_ballot_compact_workspace(n, block_dim) -> int:
     return lib().cox_ballot_compact_workspace(n, block_dim)
+
+
+def cox_ballot_compact_static(dt, width, block_dim, d_keys, n, threshold, d_out, d_count, stream) -> int:
+    return lib().cox_ballot_compact_static(dt, width, block_dim, d_keys, n, threshold, d_out, d_count, stream)
+
+
+COX_COMPACT_STATIC_SCRATCH_BYTES = 1 << 20
 
 
 def cox_match_histogram(dt, width, block_dim, d_keys, n, bins, d_hist, d_ignored, stream) -> int:
@@ -240,3 +248,4 @@ def match_histogram(keys, bins: int = 256, width: int = 32, block_dim: int = 256
 def device_status(stream=None) -> int:
     """Synchronise and read/clear the device status word (cox_device_status)."""
     return cox_device_status(stream if stream is not None else _stream(None))
+

@@ -14,6 +14,8 @@
 // j*4B + 4t .. 4t+3.  The rank of key (j, t, k) in the tile is
 //   offset(j, warp) + sum_k' popc(ballot_k'(j) & lanemask_lt) + #{k' < k kept}
 // which is its position in input order, so the result is the stable filter.
+#include <mutex>
+
 #include "cox_common.cuh"
 
 namespace cox {
@@ -224,4 +226,58 @@ extern "C" cox_status cox_ballot_compact(cox_dtype dt, int width, int block_dim,
     return launch_status();
   };
   return dt == COX_I32 ? launch(k_ballot_compact<true>) : launch(k_ballot_compact<false>);
+}
+
+// ---------------------------------------------------------------------------
+// cox_ballot_compact_static: the same compaction for callers that cannot
+// allocate device memory.  Its scratch (the ticket and the per-tile
+// look-back descriptors) lives in the fixed array below instead of a
+// caller-provided workspace.
+//
+// The array belongs to the library image: every GPU that loads libcox.so
+// holds these bytes until the process exits.  In host code the name
+// g_compact_scratch is only a host-side stand-in for the symbol, not a
+// device address, so it is never passed to a kernel; the device address is
+// looked up with cudaGetSymbolAddress once per device (on that device's first
+// call of this entry point, with the device current) and cached.
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(1) << 20;  // COX_COMPACT_STATIC_SCRATCH_BYTES
+static __device__ __align__(256) unsigned char g_compact_scratch[kStaticScratchBytes];
+
+constexpr int kStaticMaxDevices = 64;
+void* g_scratch_addr[kStaticMaxDevices];
+std::mutex g_scratch_mu;
+
+cox_status static_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return COX_ECUDA;
+  if (dev < 0 || dev >= kStaticMaxDevices) return COX_EUNSUPPORTED;
+  std::lock_guard<std::mutex> g(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_compact_scratch) != cudaSuccess || !p) return COX_ECUDA;
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return COX_OK;
+}
+
+}  // namespace
+
+extern "C" cox_status cox_ballot_compact_static(cox_dtype dt, int width, int block_dim, const void* d_keys,
+                                                int64_t n, int64_t threshold, void* d_out, int64_t* d_count,
+                                                void* stream) {
+  if (!valid_width(width) || !valid_block(block_dim) || n < 0) return COX_EINVAL;
+  if (dt != COX_I32 && dt != COX_U32) return COX_EINVAL;
+  if (!d_count || (n > 0 && (!d_keys || !d_out))) return COX_EINVAL;
+  // Larger inputs need more descriptors than the fixed scratch holds.
+  if (cox_ballot_compact_workspace(n, block_dim) > kStaticScratchBytes) return COX_ENOMEM;
+  void* scratch = nullptr;
+  const cox_status s = static_scratch(&scratch);
+  if (s != COX_OK) return s;
+  // The call zeroes the bytes it uses (ticket and descriptors), because the
+  // array still holds whatever the previous call left there.
+  return cox_ballot_compact(dt, width, block_dim, d_keys, n, threshold, d_out, d_count, scratch,
+                            kStaticScratchBytes, 0u, stream);
 }
