@@ -336,10 +336,12 @@ def run_secondary(dev, st):
     z = torch.from_numpy(inputs.zipf_keys(n, inputs.BASE_SEED + 3)).to(dev)
     hist = torch.empty(256, dtype=torch.int32, device=dev)
     ms = _time_launches(st, lambda: chk(cox.cox_match_histogram(0, 32, 256, z.data_ptr(), n, 256, hist.data_ptr(),
-                                                                None, sh)))
+                                                                None, 0, sh)))
     gbs = n * 4 / (ms * 1e-3) / 1e9
     res["match_histogram_2p28_zipf"] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3)}
     del z
+
+    res["batched_10000_uneven"] = run_batched(dev, st)
 
     # grid reduce of 2^28 fp32, compensated
     f = torch.randn(n, dtype=torch.float32, device=dev)
@@ -351,6 +353,98 @@ def run_secondary(dev, st):
     gbs = n * 4 / (ms * 1e-3) / 1e9
     res["grid_sum_2p28_fp32_comp"] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3)}
     return res
+
+
+def run_batched(dev, st, num_arrays=10_000):
+    """Batched workload: num_arrays arrays with lengths log-uniform on
+    [32, 2^20] (~1e9 elements), fp32 N(0,1) values and Zipf(1.1) keys; per
+    array a compensated sum and a 256-bin match histogram.  One persistent
+    launch (+ ordered combine) replayed from a CUDA graph, against one launch
+    per array (grid reduce + histogram) on the same stream.  Inputs are drawn
+    on the device (torch generator) to keep the setup short."""
+    import ctypes
+    import torch
+    from paper_2112_10034_gb300 import cox
+
+    def chk(s, what="batched"):
+        if s != 0:
+            raise cox.CoxError(s, what)
+
+    lens = inputs.loguniform_lengths(num_arrays, 32, 1 << 20, inputs.BASE_SEED + 3)
+    padded = (lens + 3) // 4 * 4
+    starts = np.concatenate([[0], np.cumsum(padded)[:-1]]).astype(np.int64)
+    total_padded = int(padded.sum())
+    E = int(lens.sum())
+    g = torch.Generator(device=dev)
+    g.manual_seed(inputs.BASE_SEED + 4)
+    vals = torch.randn(total_padded, generator=g, device=dev, dtype=torch.float32)
+    w = torch.arange(1, 257, dtype=torch.float64, device=dev) ** -1.1
+    cdf = torch.cumsum(w / w.sum(), 0)
+    cdf[-1] = 1.0
+    keys = torch.empty(total_padded, dtype=torch.int32, device=dev)
+    chunk = 1 << 27
+    for c0 in range(0, total_padded, chunk):
+        u = torch.rand(min(chunk, total_padded - c0), generator=g, device=dev, dtype=torch.float64)
+        keys[c0:c0 + u.numel()] = torch.searchsorted(cdf, u, right=True).to(torch.int32)
+        del u
+    pv = torch.from_numpy(vals.data_ptr() + 4 * starts).to(dev)
+    pk = torch.from_numpy(keys.data_ptr() + 4 * starts).to(dev)
+    lens_h = torch.from_numpy(lens.astype(np.int64))
+    wsb = cox.cox_batch_workspace(num_arrays)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    sums = torch.empty(num_arrays, dtype=torch.float32, device=dev)
+    sums64 = torch.empty(num_arrays, dtype=torch.float64, device=dev)
+    hists = torch.empty((num_arrays, 256), dtype=torch.int32, device=dev)
+    sh = st.cuda_stream
+    chk(cox.cox_batch_prepare(num_arrays, lens_h.data_ptr(), ws.data_ptr(), wsb, sh))
+    best = cox.cox_batch_tune()
+    best_ms = ctypes.c_float()
+    chk(cox.cox_batch_autotune(num_arrays, pv.data_ptr(), pk.data_ptr(), ws.data_ptr(), wsb, sums.data_ptr(),
+                               hists.data_ptr(), 2, None, ctypes.byref(best), ctypes.byref(best_ms), sh))
+    graph = ctypes.c_void_p()
+    chk(cox.cox_batch_graph_create(num_arrays, pv.data_ptr(), pk.data_ptr(), ctypes.addressof(best), ws.data_ptr(),
+                                   wsb, sums.data_ptr(), sums64.data_ptr(), hists.data_ptr(), ctypes.byref(graph)))
+    try:
+        ms = _time_launches(st, lambda: chk(cox.cox_graph_launch(graph, sh)), iters=20)
+    finally:
+        cox.cox_graph_destroy(graph)
+    nbytes = E * 8
+    peak, _ = _peaks()
+
+    # one launch per array: grid-scope compensated sum + match histogram
+    rws_b = cox.cox_tile_reduce_workspace(2, 1 << 20, 256)
+    rws = torch.empty(rws_b, dtype=torch.uint8, device=dev)
+    ign = torch.empty(1, dtype=torch.int64, device=dev)
+    vp, kp = vals.data_ptr(), keys.data_ptr()
+    s_p, h_p = sums.data_ptr(), hists.data_ptr()
+
+    def per_call(events=None):
+        for a in range(num_arrays):
+            L, o4 = int(lens[a]), 4 * int(starts[a])
+            chk(cox.cox_tile_reduce(0, 2, 32, 256, 2, vp + o4, s_p + 4 * a, L, 1, None, rws.data_ptr(), rws_b, sh))
+            chk(cox.cox_match_histogram(0, 32, 256, kp + o4, L, 256, h_p + 1024 * a, ign.data_ptr(), 0, sh))
+            if events is not None:
+                events[a].record(st)
+
+    per_call()  # warm-up
+    st.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(num_arrays)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t0.record(st)
+    per_call(evs)
+    evs[-1].synchronize()
+    done = np.array([t0.elapsed_time(e) for e in evs])
+    pc_ms = float(done[-1])
+    return {"arrays": num_arrays, "elements": E, "bytes": nbytes,
+            "tune": dict(zip(["block_dim", "ctas_per_sm", "width", "fp64_segments", "native_match"], best.astuple())),
+            "graph_ms": round(ms, 4), "GB/s": round(nbytes / (ms * 1e-3) / 1e9, 1),
+            "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 3),
+            "latency_ms": {"p50": round(ms, 4), "p99": round(ms, 4), "note": "every array completes with the batch"},
+            "per_call": {"ms": round(pc_ms, 3), "GB/s": round(nbytes / (pc_ms * 1e-3) / 1e9, 1),
+                         "launches": 2 * num_arrays,
+                         "latency_ms": {"p50": round(float(np.percentile(done, 50)), 3),
+                                        "p99": round(float(np.percentile(done, 99)), 3)}},
+            "speedup_vs_per_call": round(pc_ms / ms, 2)}
 
 
 # ------------------------------------------------------ CPU (oracle) legs
@@ -416,22 +510,57 @@ def run_reference(args):
 
 
 def run_profile(args):
-    """Small case for an ncu capture: the 8 scan launches per step over one
-    2^26-element input and one output (512 MiB on the device), nothing else."""
+    """Small cases for ncu captures (a few hundred MiB on the device, inputs
+    larger than L2), one op each: `scan` runs the 8 scan launches per step over
+    one 2^26-element input and one output; `compact` runs 2^26-key compactions
+    at density 0.5; `hist` runs 2^26-key Zipf match histograms; `batch` runs
+    the batched kernel on 1000 arrays of the batched length law (~1e8
+    elements)."""
     import torch
     from paper_2112_10034_gb300 import cox
     dev = torch.device("cuda", 0)
     st = torch.cuda.Stream(device=dev)
-    x = torch.from_numpy(inputs.normal_f32(N_ELEMS, inputs.BASE_SEED + 1)).to(dev)
-    out = torch.empty(N_ELEMS, dtype=torch.float32, device=dev)
-    for _ in range(args.warmup + args.steps):
-        for w, comp in VARIANTS:
-            s = cox.cox_tile_scan(cox.COX_SUM, cox.COX_F32, w, BLOCK, x.data_ptr(), out.data_ptr(), N_ELEMS,
-                                  cox.COX_F_COMPENSATED if comp else 0, st.cuda_stream)
-            if s != 0:
-                raise cox.CoxError(s, "cox_tile_scan")
+    sh = st.cuda_stream
+
+    def chk(s):
+        if s != 0:
+            raise cox.CoxError(s, args.profile)
+
+    reps = args.warmup + args.steps
+    if args.profile == "scan":
+        x = torch.from_numpy(inputs.normal_f32(N_ELEMS, inputs.BASE_SEED + 1)).to(dev)
+        out = torch.empty(N_ELEMS, dtype=torch.float32, device=dev)
+        for _ in range(reps):
+            for w, comp in VARIANTS:
+                chk(cox.cox_tile_scan(cox.COX_SUM, cox.COX_F32, w, BLOCK, x.data_ptr(), out.data_ptr(), N_ELEMS,
+                                      cox.COX_F_COMPENSATED if comp else 0, sh))
+        launches = reps * len(VARIANTS)
+    elif args.profile == "compact":
+        k = torch.from_numpy(inputs.uniform_u31(N_ELEMS, inputs.BASE_SEED + 2)).to(dev)
+        out = torch.empty(N_ELEMS, dtype=torch.int32, device=dev)
+        cnt = torch.empty(1, dtype=torch.int64, device=dev)
+        wsb = cox.cox_ballot_compact_workspace(N_ELEMS, 256)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        for _ in range(reps):
+            chk(cox.cox_ballot_compact(0, 32, 256, k.data_ptr(), N_ELEMS, inputs.density_threshold(0.5),
+                                       out.data_ptr(), cnt.data_ptr(), ws.data_ptr(), wsb, 0, sh))
+        launches = reps
+    elif args.profile == "batch":
+        lens = inputs.loguniform_lengths(1000, 32, 1 << 20, inputs.BASE_SEED + 3)
+        vals = [torch.randn(int(L), device=dev) for L in lens]
+        keys = [torch.randint(0, 256, (int(L),), device=dev, dtype=torch.int32) for L in lens]
+        b = cox.Batch(vals, keys)
+        for _ in range(reps):
+            b.run(sh)
+        launches = reps * 2
+    else:
+        z = torch.from_numpy(inputs.zipf_keys(N_ELEMS, inputs.BASE_SEED + 3)).to(dev)
+        hist = torch.empty(256, dtype=torch.int32, device=dev)
+        for _ in range(reps):
+            chk(cox.cox_match_histogram(0, 32, 256, z.data_ptr(), N_ELEMS, 256, hist.data_ptr(), None, 0, sh))
+        launches = reps
     st.synchronize()
-    print(json.dumps({"profile": "tile_scan", "launches": (args.warmup + args.steps) * len(VARIANTS)}))
+    print(json.dumps({"profile": args.profile, "launches": launches}))
 
 
 def main():
@@ -443,7 +572,8 @@ def main():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--profile", action="store_true", help="small case for ncu: scan launches only")
+    ap.add_argument("--profile", choices=["scan", "compact", "hist", "batch"], default=None,
+                    help="small single-op case for ncu captures")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -74,7 +74,8 @@ typedef enum { COX_SCOPE_TILE = 0, COX_SCOPE_BLOCK = 1, COX_SCOPE_GRID = 2 } cox
 enum {
   COX_F_COMPENSATED = 1u,  /* fp32 sums: TwoSum-compensated pairs through every stage */
   COX_F_FP64_COMBINE = 2u, /* GRID scope fp32 sum: final cross-block combine in FP64 */
-  COX_F_WS_READY = 4u      /* compaction: caller zeroed the workspace; skip the memset */
+  COX_F_WS_READY = 4u,     /* compaction: caller zeroed the workspace; skip the memset */
+  COX_F_NATIVE_MATCH = 8u  /* histograms: peer groups from the match.any.sync instruction */
 };
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -203,18 +204,101 @@ cox_status cox_ballot_compact_static(cox_dtype dt, int width, int block_dim, con
                                      int64_t threshold, void* d_out, int64_t* d_count, void* stream);
 
 /*
- * cox_match_histogram -- histogram built from __match_any_sync peer groups.
+ * cox_match_histogram -- histogram built from match_any peer groups.
  *
- * Per tile: peers = match_any(key); the lowest lane of each peer group adds
- * popc(peers) to a shared-memory bin; blocks merge into d_hist.  Same family
- * of warp functions as Section 2.2.1.
+ * Per tile: peers = match_any(key) among the lanes whose key is in [0, bins);
+ * the lowest lane of each peer group adds popc(peers) to a shared-memory bin;
+ * blocks merge into d_hist.  Same family of warp functions as Section 2.2.1.
+ * By default the peer mask comes from ceil(log2(bins)) + 1 ballots (lanes
+ * agree on a key iff they agree on every key bit), which is exactly the mask
+ * __match_any_sync returns; COX_F_NATIVE_MATCH takes it from the
+ * match.any.sync instruction instead (same result, slower on sm_103a).
  *   dt: COX_I32 or COX_U32 keys.  bins: 1..8192.
  *   d_hist: `bins` int32 counters, overwritten (zeroed by the call).
  *   d_ignored: optional int64 (may be NULL): number of keys outside [0, bins),
  *   overwritten.
+ *   flags: 0 or COX_F_NATIVE_MATCH.
  */
 cox_status cox_match_histogram(cox_dtype dt, int width, int block_dim, const void* d_keys, int64_t n,
-                               int bins, int32_t* d_hist, int64_t* d_ignored, void* stream);
+                               int bins, int32_t* d_hist, int64_t* d_ignored, unsigned flags, void* stream);
+
+/* ====================================================================== */
+/* Batched uneven arrays: per array, a compensated fp32 sum and a 256-bin   */
+/* histogram built with match_any, all arrays in one persistent launch.     */
+/* ====================================================================== */
+
+/* Launch shape of the batched kernel.  Every field must be set (or pass a
+ * NULL tune to take the library default, {512, 2, 32, 8, 0}). */
+typedef struct {
+  int block_dim;     /* threads per CTA, multiple of 32 in [64, 1024] */
+  int ctas_per_sm;   /* persistent CTAs per SM, 1..8 */
+  int width;         /* tile width of the match_any histogram step: 2..32 */
+  int fp64_segments; /* arrays split over >= this many CTAs combine in FP64 (>= 1) */
+  int native_match;  /* 1: match.any.sync instruction; 0: the same peer masks from 9 ballots */
+} cox_batch_tune;
+
+/* Bytes of device workspace for a batch of num_arrays arrays (any tune). */
+size_t cox_batch_workspace(int64_t num_arrays);
+
+/*
+ * cox_batch_prepare -- writes the batch's offset table (prefix sums of the
+ * host array h_lens[num_arrays], lengths >= 0) into d_workspace.  Copies on
+ * `stream` and synchronises it before returning, so h_lens may be freed
+ * afterwards.  Must precede cox_batch_sum_hist for this batch and workspace.
+ */
+cox_status cox_batch_prepare(int64_t num_arrays, const int64_t* h_lens, void* d_workspace,
+                             size_t workspace_bytes, void* stream);
+
+/*
+ * cox_batch_sum_hist -- for every array a (length h_lens[a] as prepared):
+ *   d_sums[a]      compensated fp32 sum of d_vals[a][0 .. len)  (fl(s + e));
+ *   d_sums64[a]    optional (may be NULL): the same sum as a double
+ *                  (s + e of the final pair, or the FP64 combine);
+ *   d_hists[a*256 + k] = #{i : d_keys[a][i] == k}, k in [0, 256) (keys
+ *                  outside are ignored); zeroed by the call.
+ * d_vals / d_keys are DEVICE arrays of num_arrays device pointers.  The grid
+ * splits the concatenation of all arrays into equal element ranges, one per
+ * persistent CTA; each CTA folds its part of each array (TwoSum pairs per
+ * thread, then a shuffle tree) and flushes per-warp match_any histograms;
+ * a second small kernel folds each array's per-CTA pairs in CTA order, in
+ * FP64 when the array spans >= tune->fp64_segments CTAs (Section 2.2.1
+ * warp functions; the paper has no batching of its own).  Results depend
+ * only on the data and the tune, never on timing.  Enqueue only: capturable
+ * in a CUDA graph.
+ */
+cox_status cox_batch_sum_hist(int64_t num_arrays, const float* const* d_vals, const int32_t* const* d_keys,
+                              const cox_batch_tune* tune, void* d_workspace, size_t workspace_bytes,
+                              float* d_sums, double* d_sums64, int32_t* d_hists, void* stream);
+
+/* An instantiated CUDA graph of one cox_batch_sum_hist call. */
+typedef struct cox_graph cox_graph;
+
+/* Captures cox_batch_sum_hist with these arguments into a graph (on a private
+ * stream) and instantiates it.  Replays read the buffers named here. */
+cox_status cox_batch_graph_create(int64_t num_arrays, const float* const* d_vals, const int32_t* const* d_keys,
+                                  const cox_batch_tune* tune, void* d_workspace, size_t workspace_bytes,
+                                  float* d_sums, double* d_sums64, int32_t* d_hists, cox_graph** out);
+cox_status cox_graph_launch(cox_graph* g, void* stream);
+void cox_graph_destroy(cox_graph* g);
+
+/*
+ * cox_batch_autotune -- times every candidate tune (block_dim 256/512/1024 x
+ * ctas_per_sm 1/2/4 x width 8/32, ballot-built peer masks) on this batch (prepared in d_workspace)
+ * with CUDA events, `reps` timed runs each, and returns the fastest in *best
+ * (and its mean milliseconds in *best_ms if non-NULL).  If cache_path is not
+ * NULL the winner is appended to that file as one line
+ * "<gpu name>|batch_sum_hist|<arrays bucket>|<elements bucket>|b,c,w,f,m|ms".
+ * Synchronises `stream`.  Overwrites the output buffers.
+ */
+cox_status cox_batch_autotune(int64_t num_arrays, const float* const* d_vals, const int32_t* const* d_keys,
+                              void* d_workspace, size_t workspace_bytes, float* d_sums, int32_t* d_hists,
+                              int reps, const char* cache_path, cox_batch_tune* best, float* best_ms,
+                              void* stream);
+
+/* Looks up a tune for (num_arrays, total elements) in a cache file written by
+ * cox_batch_autotune on the current GPU.  COX_EINVAL if none matches. */
+cox_status cox_batch_tune_lookup(const char* cache_path, int64_t num_arrays, int64_t total_elems,
+                                 cox_batch_tune* tune);
 
 /*
  * cox_device_status -- synchronises `stream`, then reads and clears the

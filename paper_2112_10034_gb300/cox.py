@@ -22,7 +22,7 @@ COX_SUM, COX_MIN, COX_MAX, COX_AND, COX_OR, COX_XOR = range(6)
 (COX_SHFL_IDX, COX_SHFL_UP, COX_SHFL_DOWN, COX_SHFL_XOR,
  COX_BALLOT, COX_ANY, COX_ALL, COX_MATCH_ANY) = range(8)
 COX_SCOPE_TILE, COX_SCOPE_BLOCK, COX_SCOPE_GRID = 0, 1, 2
-COX_F_COMPENSATED, COX_F_FP64_COMBINE, COX_F_WS_READY = 1, 2, 4
+COX_F_COMPENSATED, COX_F_FP64_COMBINE, COX_F_WS_READY, COX_F_NATIVE_MATCH = 1, 2, 4, 8
 FULL_MASK = 0xFFFFFFFF
 
 _P = ctypes.c_void_p
@@ -42,7 +42,15 @@ SIGNATURES = {
     "cox_ballot_compact": (_I, [_I, _I, _I, _P, _I64, _I64, _P, _P, _P, _SZ, _U, _P]),
     "cox_ballot_compact_workspace": (_SZ, [_I64, _I]),
     "cox_ballot_compact_static": (_I, [_I, _I, _I, _P, _I64, _I64, _P, _P, _P]),
-    "cox_match_histogram": (_I, [_I, _I, _I, _P, _I64, _I, _P, _P, _P]),
+    "cox_match_histogram": (_I, [_I, _I, _I, _P, _I64, _I, _P, _P, _U, _P]),
+    "cox_batch_workspace": (_SZ, [_I64]),
+    "cox_batch_prepare": (_I, [_I64, _P, _P, _SZ, _P]),
+    "cox_batch_sum_hist": (_I, [_I64, _P, _P, _P, _P, _SZ, _P, _P, _P, _P]),
+    "cox_batch_graph_create": (_I, [_I64, _P, _P, _P, _P, _SZ, _P, _P, _P, _P]),
+    "cox_graph_launch": (_I, [_P, _P]),
+    "cox_graph_destroy": (None, [_P]),
+    "cox_batch_autotune": (_I, [_I64, _P, _P, _P, _SZ, _P, _P, _I, ctypes.c_char_p, _P, _P, _P]),
+    "cox_batch_tune_lookup": (_I, [ctypes.c_char_p, _I64, _I64, _P]),
     "cox_device_status": (_I, [_P]),
     "cox_set_spin_limit": (None, [ctypes.c_uint32]),
 }
@@ -115,8 +123,53 @@ def cox_ballot_compact_static(dt, width, block_dim, d_keys, n, threshold, d_out,
 COX_COMPACT_STATIC_SCRATCH_BYTES = 1 << 20
 
 
-def cox_match_histogram(dt, width, block_dim, d_keys, n, bins, d_hist, d_ignored, stream) -> int:
-    return lib().cox_match_histogram(dt, width, block_dim, d_keys, n, bins, d_hist, d_ignored, stream)
+def cox_match_histogram(dt, width, block_dim, d_keys, n, bins, d_hist, d_ignored, flags, stream) -> int:
+    return lib().cox_match_histogram(dt, width, block_dim, d_keys, n, bins, d_hist, d_ignored, flags, stream)
+
+
+class cox_batch_tune(ctypes.Structure):
+    """Launch shape of the batched kernel (mirrors the C struct)."""
+    _fields_ = [("block_dim", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("width", ctypes.c_int),
+                ("fp64_segments", ctypes.c_int), ("native_match", ctypes.c_int)]
+
+    def astuple(self):
+        return (self.block_dim, self.ctas_per_sm, self.width, self.fp64_segments, self.native_match)
+
+
+def cox_batch_workspace(num_arrays) -> int:
+    return lib().cox_batch_workspace(num_arrays)
+
+
+def cox_batch_prepare(num_arrays, h_lens, d_ws, ws_bytes, stream) -> int:
+    return lib().cox_batch_prepare(num_arrays, h_lens, d_ws, ws_bytes, stream)
+
+
+def cox_batch_sum_hist(num_arrays, d_vals, d_keys, tune, d_ws, ws_bytes, d_sums, d_sums64, d_hists, stream) -> int:
+    return lib().cox_batch_sum_hist(num_arrays, d_vals, d_keys, tune, d_ws, ws_bytes, d_sums, d_sums64, d_hists,
+                                    stream)
+
+
+def cox_batch_graph_create(num_arrays, d_vals, d_keys, tune, d_ws, ws_bytes, d_sums, d_sums64, d_hists, out) -> int:
+    return lib().cox_batch_graph_create(num_arrays, d_vals, d_keys, tune, d_ws, ws_bytes, d_sums, d_sums64, d_hists,
+                                        out)
+
+
+def cox_graph_launch(g, stream) -> int:
+    return lib().cox_graph_launch(g, stream)
+
+
+def cox_graph_destroy(g) -> None:
+    lib().cox_graph_destroy(g)
+
+
+def cox_batch_autotune(num_arrays, d_vals, d_keys, d_ws, ws_bytes, d_sums, d_hists, reps, cache_path, best, best_ms,
+                       stream) -> int:
+    return lib().cox_batch_autotune(num_arrays, d_vals, d_keys, d_ws, ws_bytes, d_sums, d_hists, reps, cache_path,
+                                    best, best_ms, stream)
+
+
+def cox_batch_tune_lookup(cache_path, num_arrays, total_elems, tune) -> int:
+    return lib().cox_batch_tune_lookup(cache_path, num_arrays, total_elems, tune)
 
 
 def cox_device_status(stream) -> int:
@@ -234,14 +287,16 @@ def ballot_compact(keys, threshold: int, width: int = 32, block_dim: int = 256, 
     return out, count
 
 
-def match_histogram(keys, bins: int = 256, width: int = 32, block_dim: int = 256, unsigned: bool = False):
+def match_histogram(keys, bins: int = 256, width: int = 32, block_dim: int = 256, unsigned: bool = False,
+                    native_match: bool = False):
     """Match-any histogram (cox_match_histogram).  Returns (hist int32[bins], ignored int64[1])."""
     t = _torch()
     keys = _dev_tensor(keys)
     hist = t.empty(bins, dtype=t.int32, device=keys.device)
     ign = t.empty(1, dtype=t.int64, device=keys.device)
     _check(cox_match_histogram(COX_U32 if unsigned else COX_I32, width, block_dim, keys.data_ptr(), keys.numel(),
-                               bins, hist.data_ptr(), ign.data_ptr(), _stream(keys.device)), "cox_match_histogram")
+                               bins, hist.data_ptr(), ign.data_ptr(), COX_F_NATIVE_MATCH if native_match else 0,
+                               _stream(keys.device)), "cox_match_histogram")
     return hist, ign
 
 
@@ -249,3 +304,85 @@ def device_status(stream=None) -> int:
     """Synchronise and read/clear the device status word (cox_device_status)."""
     return cox_device_status(stream if stream is not None else _stream(None))
 
+
+class Batch:
+    """A prepared batch of uneven arrays for cox_batch_sum_hist.
+
+    `vals` / `keys`: lists of 1-D CUDA tensors (float32 values, int32 keys),
+    array a being vals[a] with keys[a] of the same length.  Holds the device
+    pointer tables, the workspace and the outputs (sums fp32, sums64 fp64,
+    hists int32 [A, 256]); run() enqueues one batched call, graph() captures
+    one into a CUDA graph for replay.
+    """
+
+    def __init__(self, vals, keys, tune=None):
+        t = _torch()
+        if len(vals) != len(keys) or not vals:
+            raise ValueError("vals and keys must be non-empty lists of the same length")
+        dev = vals[0].device
+        self.A = len(vals)
+        self.vals, self.keys = vals, keys  # keep the tensors alive
+        lens = [int(v.numel()) for v in vals]
+        for v, k in zip(vals, keys):
+            if v.numel() != k.numel() or v.dtype != t.float32 or k.dtype != t.int32:
+                raise ValueError("each array needs float32 values and int32 keys of equal length")
+        self.lens = t.tensor(lens, dtype=t.int64)
+        self.total = sum(lens)
+        self.pv = t.tensor([v.data_ptr() for v in vals], dtype=t.int64, device=dev)
+        self.pk = t.tensor([k.data_ptr() for k in keys], dtype=t.int64, device=dev)
+        self.ws_bytes = cox_batch_workspace(self.A)
+        self.ws = t.empty(self.ws_bytes, dtype=t.uint8, device=dev)
+        self.sums = t.empty(self.A, dtype=t.float32, device=dev)
+        self.sums64 = t.empty(self.A, dtype=t.float64, device=dev)
+        self.hists = t.empty((self.A, 256), dtype=t.int32, device=dev)
+        self.tune = None
+        if tune is not None:
+            self.tune = cox_batch_tune(*tune) if not isinstance(tune, cox_batch_tune) else tune
+        self.stream = _stream(dev)
+        _check(cox_batch_prepare(self.A, self.lens.data_ptr(), self.ws.data_ptr(), self.ws_bytes, self.stream),
+               "cox_batch_prepare")
+
+    def _tune_ptr(self):
+        return ctypes.addressof(self.tune) if self.tune is not None else None
+
+    def run(self, stream=None):
+        _check(cox_batch_sum_hist(self.A, self.pv.data_ptr(), self.pk.data_ptr(), self._tune_ptr(),
+                                  self.ws.data_ptr(), self.ws_bytes, self.sums.data_ptr(), self.sums64.data_ptr(),
+                                  self.hists.data_ptr(), stream if stream is not None else self.stream),
+               "cox_batch_sum_hist")
+        return self.sums, self.sums64, self.hists
+
+    def graph(self):
+        g = ctypes.c_void_p()
+        _check(cox_batch_graph_create(self.A, self.pv.data_ptr(), self.pk.data_ptr(), self._tune_ptr(),
+                                      self.ws.data_ptr(), self.ws_bytes, self.sums.data_ptr(), self.sums64.data_ptr(),
+                                      self.hists.data_ptr(), ctypes.byref(g)), "cox_batch_graph_create")
+        return Graph(g)
+
+    def autotune(self, reps: int = 3, cache_path=None):
+        best = cox_batch_tune()
+        ms = ctypes.c_float()
+        _check(cox_batch_autotune(self.A, self.pv.data_ptr(), self.pk.data_ptr(), self.ws.data_ptr(), self.ws_bytes,
+                                  self.sums.data_ptr(), self.hists.data_ptr(), reps,
+                                  cache_path.encode() if cache_path else None, ctypes.byref(best), ctypes.byref(ms),
+                                  self.stream), "cox_batch_autotune")
+        self.tune = best
+        return best, ms.value
+
+
+class Graph:
+    """An instantiated CUDA graph from the library (cox_graph)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def launch(self, stream=None):
+        _check(cox_graph_launch(self.handle, stream if stream is not None else _stream(None)), "cox_graph_launch")
+
+    def __del__(self):
+        try:
+            if self.handle:
+                cox_graph_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass

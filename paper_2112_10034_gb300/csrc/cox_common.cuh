@@ -218,6 +218,25 @@ __device__ __forceinline__ typename R::V block_reduce32(typename R::V v, typenam
   return acc;
 }
 
+// Peer mask of __match_any_sync(full, key) among the lanes with `in` set,
+// for keys that fit in BITS bits, built from BITS + 1 warp ballots: two lanes
+// hold the same key exactly when they agree on every bit.  On sm_103a the
+// match.sync instruction costs roughly 40 SM cycles per warp instruction and
+// grows with the number of distinct keys, while a ballot is a plain vote, so
+// this form is the fast one for histogram-sized keys.  Lanes without `in`
+// get an arbitrary mask and must not use it.
+template <int BITS>
+__device__ __forceinline__ unsigned match_any_bits(uint32_t key, bool in) {
+  unsigned peers = __ballot_sync(kFull, in);
+#pragma unroll
+  for (int i = 0; i < BITS; ++i) {
+    const bool b = (key >> i) & 1u;
+    const unsigned m = __ballot_sync(kFull, b);
+    peers &= b ? m : ~m;
+  }
+  return peers;
+}
+
 // ------------------------------------------------------------ staging layer
 // A warp chunk is ROWS rows of 32 consecutive 32-bit elements; after loading,
 // lane l holds row[r] = element base + 32 r + l (the paper's lane numbering:

@@ -1,32 +1,40 @@
-// cox_match_histogram: histogram from __match_any_sync peer groups.
+// cox_match_histogram: histogram from match_any peer groups.
 //
 // Per warp step every lane holds one key; peers = match_any(key) restricted to
-// the lane's width-W tile and to lanes that hold a key; the lowest peer (the
-// group's leader) adds popc(peers) to a shared-memory bin, so equal keys in a
-// tile cost one shared atomic instead of one each.  Keys outside [0, bins)
-// are counted as ignored.  Shared histograms are per warp when they fit (no
-// cross-warp contention on hot bins, e.g. Zipf keys), else per CTA; each CTA
-// merges its non-zero bins into the output with global atomics.  Integer
-// counts: the result does not depend on which lanes group together.
+// the lane's width-W tile and to lanes whose key is in [0, bins); the lowest
+// peer (the group's leader) adds popc(peers) to a shared-memory bin, so equal
+// keys in a tile cost one shared atomic instead of one each.  Keys outside
+// [0, bins) are counted as ignored.  The peer mask comes from ballots over
+// the key bits (match_any_bits) or, with COX_F_NATIVE_MATCH, from the
+// match.any.sync instruction; both give the same mask.  Shared histograms are
+// per warp when they fit (no cross-warp contention on hot bins, e.g. Zipf
+// keys), else per CTA; each CTA merges its non-zero bins into the output with
+// global atomics.  Integer counts: exact whatever the grouping.
 #include "cox_common.cuh"
 
 namespace cox {
 
-template <int W>
+// One warp step: every lane holds one key.  Keys in [0, bins) form peer
+// groups (match_any restricted to the lane's width-W tile and to in-range
+// lanes); the lowest lane of each group adds the group's size to its bin.
+// Valid keys outside the range are counted by lane 0 through one ballot --
+// the same total as summing their peer groups.
+template <int W, int BITS, bool NATIVE>
 __device__ __forceinline__ void hist_step(uint32_t key, bool valid, uint32_t bins, uint32_t* my,
                                           uint32_t& ign) {
   const int lane = lane_id();
   const unsigned tmask = W == 32 ? kFull : (((1u << W) - 1u) << (lane & ~(W - 1)));
-  const unsigned vb = __ballot_sync(kFull, valid);
-  const unsigned peers = __match_any_sync(kFull, key) & vb & tmask;
-  if (valid && (peers & lanemask_lt()) == 0u) {
-    const uint32_t c = __popc(peers);
-    if (key < bins) atomicAdd(my + key, c);
-    else ign += c;
-  }
+  const bool in = valid && key < bins;
+  unsigned peers;
+  if constexpr (NATIVE) peers = __match_any_sync(kFull, key) & __ballot_sync(kFull, in);
+  else peers = match_any_bits<BITS>(key, in);
+  peers &= tmask;
+  if (in && (peers & lanemask_lt()) == 0u) atomicAdd(my + key, (uint32_t)__popc(peers));
+  const unsigned out = __ballot_sync(kFull, valid && !in);
+  if (lane == 0) ign += __popc(out);
 }
 
-template <int W>
+template <int W, int BITS, bool NATIVE>
 __global__ void __launch_bounds__(1024) k_match_hist(const uint32_t* __restrict__ keys, int64_t n, uint32_t bins,
                                                      int per_warp, int32_t* __restrict__ hist,
                                                      unsigned long long* ignored, int vec) {
@@ -47,14 +55,14 @@ __global__ void __launch_bounds__(1024) k_match_hist(const uint32_t* __restrict_
     for (; s + gws < nsteps && (s + gws + 1) * 128 <= n; s += 2 * gws) {  // two loads in flight
       const uint4 a = __ldcs(reinterpret_cast<const uint4*>(keys + s * 128) + lane);
       const uint4 b = __ldcs(reinterpret_cast<const uint4*>(keys + (s + gws) * 128) + lane);
-      hist_step<W>(a.x, true, bins, my, ign);
-      hist_step<W>(a.y, true, bins, my, ign);
-      hist_step<W>(a.z, true, bins, my, ign);
-      hist_step<W>(a.w, true, bins, my, ign);
-      hist_step<W>(b.x, true, bins, my, ign);
-      hist_step<W>(b.y, true, bins, my, ign);
-      hist_step<W>(b.z, true, bins, my, ign);
-      hist_step<W>(b.w, true, bins, my, ign);
+      hist_step<W, BITS, NATIVE>(a.x, true, bins, my, ign);
+      hist_step<W, BITS, NATIVE>(a.y, true, bins, my, ign);
+      hist_step<W, BITS, NATIVE>(a.z, true, bins, my, ign);
+      hist_step<W, BITS, NATIVE>(a.w, true, bins, my, ign);
+      hist_step<W, BITS, NATIVE>(b.x, true, bins, my, ign);
+      hist_step<W, BITS, NATIVE>(b.y, true, bins, my, ign);
+      hist_step<W, BITS, NATIVE>(b.z, true, bins, my, ign);
+      hist_step<W, BITS, NATIVE>(b.w, true, bins, my, ign);
     }
   }
   for (; s < nsteps; s += gws) {
@@ -73,10 +81,8 @@ __global__ void __launch_bounds__(1024) k_match_hist(const uint32_t* __restrict_
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) hist_step<W>(k[q], v[q], bins, my, ign);
+    for (int q = 0; q < 4; ++q) hist_step<W, BITS, NATIVE>(k[q], v[q], bins, my, ign);
   }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) ign += __shfl_xor_sync(kFull, ign, off);
   if (lane == 0 && ign) atomicAdd(&s_ign, ign);
   __syncthreads();
   for (uint32_t b = threadIdx.x; b < bins; b += blockDim.x) {
@@ -91,15 +97,47 @@ __global__ void __launch_bounds__(1024) k_match_hist(const uint32_t* __restrict_
   if (threadIdx.x == 0 && s_ign && ignored) atomicAdd(ignored, (unsigned long long)s_ign);
 }
 
+template <int W, int BITS, bool NATIVE>
+static cox_status launch_hist(const void* d_keys, int64_t n, int bins, int block_dim, int per_warp, size_t smem,
+                              int32_t* d_hist, int64_t* d_ignored, cudaStream_t st) {
+  auto k = k_match_hist<W, BITS, NATIVE>;
+  const int nw = block_dim / 32;
+  static int gmax[33][49];  // by warps per CTA and shared KiB
+  int& g = gmax[nw][(smem + 1023) / 1024];
+  if (g == 0) g = persistent_grid(k, block_dim, smem, 1 << 30);
+  const int64_t steps = (n + 127) / 128;
+  const int64_t ctas = (steps + nw - 1) / nw;
+  k<<<(int)(ctas < g ? ctas : g), block_dim, smem, st>>>(static_cast<const uint32_t*>(d_keys), n, (uint32_t)bins,
+                                                         per_warp, d_hist,
+                                                         reinterpret_cast<unsigned long long*>(d_ignored),
+                                                         aligned16(d_keys));
+  return launch_status();
+}
+
+template <bool NATIVE>
+static cox_status dispatch_hist(int width, const void* d_keys, int64_t n, int bins, int block_dim, int per_warp,
+                                size_t smem, int32_t* d_hist, int64_t* d_ignored, cudaStream_t st) {
+  return with_width(width, [&](auto w) {
+    constexpr int W = decltype(w)::value;
+    if (NATIVE || bins <= 256) return launch_hist<W, 8, NATIVE>(d_keys, n, bins, block_dim, per_warp, smem, d_hist,
+                                                                 d_ignored, st);
+    if (bins <= 1024) return launch_hist<W, 10, NATIVE>(d_keys, n, bins, block_dim, per_warp, smem, d_hist,
+                                                         d_ignored, st);
+    return launch_hist<W, 13, NATIVE>(d_keys, n, bins, block_dim, per_warp, smem, d_hist, d_ignored, st);
+  });
+}
+
 }  // namespace cox
 
 using namespace cox;
 
 extern "C" cox_status cox_match_histogram(cox_dtype dt, int width, int block_dim, const void* d_keys, int64_t n,
-                                          int bins, int32_t* d_hist, int64_t* d_ignored, void* stream) {
+                                          int bins, int32_t* d_hist, int64_t* d_ignored, unsigned flags,
+                                          void* stream) {
   if (!valid_width(width) || !valid_block(block_dim) || n < 0) return COX_EINVAL;
   if (dt != COX_I32 && dt != COX_U32) return COX_EINVAL;
   if (bins < 1 || bins > 8192 || !d_hist || (n > 0 && !d_keys)) return COX_EINVAL;
+  if (flags & ~(unsigned)COX_F_NATIVE_MATCH) return COX_EINVAL;
   cudaStream_t st = as_stream(stream);
   if (cudaMemsetAsync(d_hist, 0, (size_t)bins * sizeof(int32_t), st) != cudaSuccess) return COX_ECUDA;
   if (d_ignored && cudaMemsetAsync(d_ignored, 0, sizeof(int64_t), st) != cudaSuccess) return COX_ECUDA;
@@ -107,17 +145,7 @@ extern "C" cox_status cox_match_histogram(cox_dtype dt, int width, int block_dim
   const int nw = block_dim / 32;
   const int per_warp = (size_t)nw * bins * 4 <= 48 * 1024;
   const size_t smem = (size_t)(per_warp ? nw * bins : bins) * 4;
-  const int vec = aligned16(d_keys);
-  return with_width(width, [&](auto w) {
-    auto k = k_match_hist<decltype(w)::value>;
-    static int gmax[33][49];  // by warps per CTA and shared KiB
-    int& g = gmax[nw][(smem + 1023) / 1024];
-    if (g == 0) g = persistent_grid(k, block_dim, smem, 1 << 30);
-    const int64_t steps = (n + 127) / 128;
-    const int64_t ctas = (steps + nw - 1) / nw;
-    k<<<(int)(ctas < g ? ctas : g), block_dim, smem, st>>>(static_cast<const uint32_t*>(d_keys), n,
-                                                           (uint32_t)bins, per_warp, d_hist,
-                                                           reinterpret_cast<unsigned long long*>(d_ignored), vec);
-    return launch_status();
-  });
+  if (flags & COX_F_NATIVE_MATCH)
+    return dispatch_hist<true>(width, d_keys, n, bins, block_dim, per_warp, smem, d_hist, d_ignored, st);
+  return dispatch_hist<false>(width, d_keys, n, bins, block_dim, per_warp, smem, d_hist, d_ignored, st);
 }

@@ -88,5 +88,6 @@ def test_host_validation(cox):
     assert cox.cox_ballot_compact(0, 32, 256, 16, 10, 5, 16, None, 16, 4096, 0, None) == E
     assert cox.cox_ballot_compact(0, 32, 256, 16, 10, 5, 16, 16, 16, 8, 0, None) == cox.COX_ENOMEM
     # histogram bins range
-    assert cox.cox_match_histogram(0, 32, 256, 16, 10, 0, 16, None, None) == E
-    assert cox.cox_match_histogram(0, 32, 256, 16, 10, 8193, 16, None, None) == E
+    assert cox.cox_match_histogram(0, 32, 256, 16, 10, 0, 16, None, 0, None) == E
+    assert cox.cox_match_histogram(0, 32, 256, 16, 10, 8193, 16, None, 0, None) == E
+    assert cox.cox_match_histogram(0, 32, 256, 16, 10, 256, 16, None, 16, None) == E

@@ -299,10 +299,11 @@ def test_histogram_is_bit_exact(cox, W, bins):
         z = inputs.zipf_keys(n, seed=n + W, bins=min(bins, 256))
         z[::13] = -1
         z[5::17] = bins + 3
-        hist, ign = cox.match_histogram(dev(z), bins=bins, width=W, block_dim=B)
         want, wign = o.match_histogram(W, B, z, bins)
-        np.testing.assert_array_equal(host(hist), want)
-        assert int(ign.item()) == wign
+        for native in (False, True):
+            hist, ign = cox.match_histogram(dev(z), bins=bins, width=W, block_dim=B, native_match=native)
+            np.testing.assert_array_equal(host(hist), want)
+            assert int(ign.item()) == wign
 
 
 # ------------------------------------------------------------ full sizes
