@@ -330,6 +330,15 @@ def run_secondary(dev, st):
         comp[str(d)] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3),
                         "density": round(kept / n, 5)}
     res["compaction_2p28_int32"] = comp
+    t = inputs.density_threshold(0.5)
+    sweep = {}
+    for blk in (512, 1024):  # tile = block x 16 keys
+        wsb2 = cox.cox_ballot_compact_workspace(n, blk)
+        ms = _time_launches(st, lambda: chk(cox.cox_ballot_compact(0, 32, blk, k.data_ptr(), n, t, o.data_ptr(),
+                                                                   cnt.data_ptr(), ws.data_ptr(), wsb2, 0, sh)))
+        gbs = (n * 4 + int(cnt.item()) * 4) / (ms * 1e-3) / 1e9
+        sweep[str(blk)] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3)}
+    res["compaction_2p28_int32_d0.5_by_block"] = sweep
     del k, o
 
     # match histogram of 2^28 Zipf(1.1) keys into 256 bins
@@ -342,6 +351,7 @@ def run_secondary(dev, st):
     del z
 
     res["batched_10000_uneven"] = run_batched(dev, st)
+    res["serving"] = run_serving(dev)
 
     # grid reduce of 2^28 fp32, compensated
     f = torch.randn(n, dtype=torch.float32, device=dev)
@@ -445,6 +455,74 @@ def run_batched(dev, st, num_arrays=10_000):
                          "latency_ms": {"p50": round(float(np.percentile(done, 50)), 3),
                                         "p99": round(float(np.percentile(done, 99)), 3)}},
             "speedup_vs_per_call": round(pc_ms / ms, 2)}
+
+
+def run_serving(dev, rates=(1e3, 1e4, 1e5, 3e5, 1e6), count=1000, budget=8 << 30):
+    """Serving workload: a Poisson stream of requests -- 1/3 reduce (half fp32
+    compensated, half int32), 1/3 compensated fp32 tile scans (width 32), 1/3
+    int32 compactions at density 0.5 -- with sizes log-uniform on [1K, 16M]
+    elements, over an 8 GB admission budget, at each arrival rate: the
+    continuous-batching server against one launch per request (same trace).
+    Inputs are windows of 2^28-element device pools drawn by torch."""
+    import torch
+    from paper_2112_10034_gb300 import cox
+    pool_n = 1 << 28
+    g = torch.Generator(device=dev)
+    g.manual_seed(inputs.BASE_SEED + 5)
+    pf = torch.randn(pool_n, generator=g, device=dev, dtype=torch.float32)
+    pi = torch.randint(-1000, 1001, (pool_n,), generator=g, device=dev, dtype=torch.int32)
+    pk = torch.randint(0, 2**31 - 1, (pool_n,), generator=g, device=dev, dtype=torch.int32)
+    thr = inputs.density_threshold(0.5)
+    out = {}
+    for rate in rates:
+        seed = inputs.BASE_SEED + 50 + int(np.log10(rate) * 10)
+        sizes = inputs.loguniform_lengths(count, 1024, 1 << 24, seed)
+        kinds = inputs.choice(count, 3, seed + 1)
+        offs = inputs.choice(count, pool_n, seed + 2)
+        arrivals = inputs.poisson_arrivals(count, rate, seed + 3)
+        items, nbytes = [], 0
+        for i in range(count):
+            n = int(sizes[i])
+            o4 = int(min(offs[i], pool_n - n)) // 4 * 4
+            if kinds[i] == 0:
+                if i % 2:
+                    r = cox.cox_request(cox.COX_REQ_REDUCE, cox.COX_F32, 32, cox.COX_F_COMPENSATED, n, 0,
+                                        pf.data_ptr() + 4 * o4)
+                else:
+                    r = cox.cox_request(cox.COX_REQ_REDUCE, cox.COX_I32, 32, 0, n, 0, pi.data_ptr() + 4 * o4)
+                nbytes += 4 * n
+            elif kinds[i] == 1:
+                r = cox.cox_request(cox.COX_REQ_SCAN, cox.COX_F32, 32, cox.COX_F_COMPENSATED, n, 0,
+                                    pf.data_ptr() + 4 * o4)
+                nbytes += 8 * n
+            else:
+                r = cox.cox_request(cox.COX_REQ_COMPACT, cox.COX_I32, 32, 0, n, thr, pk.data_ptr() + 4 * o4)
+                nbytes += 6 * n
+            items.append((float(arrivals[i]), r))
+        srv = cox.Server(budget, max_requests=1024)
+        try:
+            srv.run_trace(items[:50])  # warm-up
+            st0 = srv.stats()
+            lat, wall = srv.run_trace(items)
+            st = srv.stats()
+            st["batches"] -= st0["batches"]
+        finally:
+            srv.close()
+        cox.percall_run_trace(items[:50])
+        lat2, wall2 = cox.percall_run_trace(items)
+        lat, lat2 = np.array(lat) * 1e3, np.array(lat2) * 1e3
+        out[f"{rate:.0e}"] = {
+            "offered_req_per_s": rate,
+            "server": {"req_per_s": round(count / wall, 1), "GB/s": round(nbytes / wall / 1e9, 1),
+                       "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                       "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                       "batches": st["batches"], "max_batch": st["max_batch"],
+                       "peak_bytes": st["peak_bytes"]},
+            "per_call": {"req_per_s": round(count / wall2, 1), "GB/s": round(nbytes / wall2 / 1e9, 1),
+                         "p50_ms": round(float(np.percentile(lat2, 50)), 3),
+                         "p99_ms": round(float(np.percentile(lat2, 99)), 3)}}
+    return {"requests_per_rate": count, "budget_bytes": budget, "sizes": "log-uniform [1K, 16M]",
+            "rates": out}
 
 
 # ------------------------------------------------------ CPU (oracle) legs

@@ -300,6 +300,104 @@ cox_status cox_batch_autotune(int64_t num_arrays, const float* const* d_vals, co
 cox_status cox_batch_tune_lookup(const char* cache_path, int64_t num_arrays, int64_t total_elems,
                                  cox_batch_tune* tune);
 
+/* ====================================================================== */
+/* Request server: continuous batching of reduce / scan / compact requests */
+/* ====================================================================== */
+
+typedef enum { COX_REQ_REDUCE = 0, COX_REQ_SCAN = 1, COX_REQ_COMPACT = 2 } cox_req_kind;
+
+/* One request.  REDUCE: the sum of all n elements (COX_F32, compensated with
+ * COX_F_COMPENSATED, or COX_I32 wrapping); output one element followed by the
+ * fp32 low word.  SCAN: tile inclusive sum scan of width `width` (COX_F32 or
+ * COX_I32), n elements out.  COMPACT: keys < threshold in input order
+ * (COX_I32 signed or COX_U32 unsigned compare), up to n elements out. */
+typedef struct {
+  cox_req_kind kind;
+  cox_dtype dt;
+  int width;
+  unsigned flags;
+  int64_t n;            /* >= 1 */
+  int64_t threshold;    /* COMPACT only */
+  const void* d_in;     /* device input, caller-owned, valid until the request completes */
+} cox_request;
+
+typedef struct cox_server cox_server;
+
+typedef struct {
+  int64_t submitted, completed, failed;
+  int64_t batches;      /* persistent launches so far */
+  int64_t max_batch;    /* most requests in one launch */
+  size_t budget_bytes;  /* admission budget */
+  size_t used_bytes;    /* held by admitted, unreleased requests */
+  size_t peak_bytes;    /* most ever held */
+  int64_t queued;       /* submitted, waiting for admission */
+} cox_server_stats;
+
+/*
+ * cox_server_create -- a server on the current device with an arena of
+ * budget_bytes of device memory (allocated here, once) and at most
+ * max_requests admitted requests at a time.  A scheduler thread admits
+ * queued requests in arrival order while the arena has room for their
+ * output and workspace (plus their input, counted as held) and a slot is
+ * free; it packs every admitted request not yet launched into one
+ * persistent kernel -- each request cut into tiles of 4096 elements that
+ * CTAs take from an atomic counter in request order -- on one of three
+ * streams, so a batch launched while another runs overlaps with it on the
+ * device; and it marks requests done when their batch's event fires.
+ * Each request's arithmetic depends only on the request (its tiles, its
+ * fixed-order combine), never on what else shares its launch.
+ */
+cox_status cox_server_create(size_t budget_bytes, int max_requests, cox_server** out);
+
+/* Queues a request; COX_ENOMEM if it could never fit the budget. */
+cox_status cox_server_submit(cox_server* s, const cox_request* req, uint64_t* ticket);
+
+/* *done = 1 once the request's results are on the device. */
+cox_status cox_server_poll(cox_server* s, uint64_t ticket, int* done);
+
+/* Blocks until the request is done or timeout_s passes (COX_ETIMEOUT). */
+cox_status cox_server_wait(cox_server* s, uint64_t ticket, double timeout_s);
+
+/* Device pointer of a done request's output (valid until release) and its
+ * element count (REDUCE 1, SCAN n, COMPACT the kept count, read from the
+ * device with a synchronous copy). */
+cox_status cox_server_result(cox_server* s, uint64_t ticket, void** d_out, int64_t* count);
+
+/* Frees a done request's arena memory and slot. */
+cox_status cox_server_release(cox_server* s, uint64_t ticket);
+
+cox_status cox_server_get_stats(cox_server* s, cox_server_stats* st);
+
+/* Stops the scheduler after the work in flight and frees the arena. */
+void cox_server_destroy(cox_server* s);
+
+/* A request of a replayed trace: submitted arrival_s seconds after the start. */
+typedef struct {
+  double arrival_s;
+  cox_request req;
+} cox_trace_item;
+
+/*
+ * cox_server_run_trace -- replays a trace (arrival times non-decreasing)
+ * through the server from the calling thread (busy-waiting to each arrival),
+ * releases every request as it completes, and writes latency_s[i] =
+ * completion - arrival for each item and *wall_s = time to the last
+ * completion.
+ */
+cox_status cox_server_run_trace(cox_server* s, const cox_trace_item* items, int64_t count, double* latency_s,
+                                double* wall_s);
+
+/*
+ * cox_percall_run_trace -- the same trace with one launch per request: each
+ * request goes to cox_tile_reduce (GRID), cox_tile_scan or
+ * cox_ballot_compact on one stream as it arrives, outputs and workspaces
+ * carved from d_scratch (scratch_bytes >= cox_percall_scratch(max n));
+ * latency as above.
+ */
+size_t cox_percall_scratch(int64_t max_n);
+cox_status cox_percall_run_trace(const cox_trace_item* items, int64_t count, void* d_scratch, size_t scratch_bytes,
+                                 double* latency_s, double* wall_s);
+
 /*
  * cox_device_status -- synchronises `stream`, then reads and clears the
  * device-side status word of the current device.  Returns COX_ETIMEOUT if

@@ -51,6 +51,17 @@ SIGNATURES = {
     "cox_graph_destroy": (None, [_P]),
     "cox_batch_autotune": (_I, [_I64, _P, _P, _P, _SZ, _P, _P, _I, ctypes.c_char_p, _P, _P, _P]),
     "cox_batch_tune_lookup": (_I, [ctypes.c_char_p, _I64, _I64, _P]),
+    "cox_server_create": (_I, [_SZ, _I, _P]),
+    "cox_server_submit": (_I, [_P, _P, _P]),
+    "cox_server_poll": (_I, [_P, ctypes.c_uint64, _P]),
+    "cox_server_wait": (_I, [_P, ctypes.c_uint64, ctypes.c_double]),
+    "cox_server_result": (_I, [_P, ctypes.c_uint64, _P, _P]),
+    "cox_server_release": (_I, [_P, ctypes.c_uint64]),
+    "cox_server_get_stats": (_I, [_P, _P]),
+    "cox_server_destroy": (None, [_P]),
+    "cox_server_run_trace": (_I, [_P, _P, _I64, _P, _P]),
+    "cox_percall_scratch": (_SZ, [_I64]),
+    "cox_percall_run_trace": (_I, [_P, _I64, _P, _SZ, _P, _P]),
     "cox_device_status": (_I, [_P]),
     "cox_set_spin_limit": (None, [ctypes.c_uint32]),
 }
@@ -386,3 +397,127 @@ class Graph:
                 self.handle = None
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ server
+COX_REQ_REDUCE, COX_REQ_SCAN, COX_REQ_COMPACT = 0, 1, 2
+
+
+class cox_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("dt", ctypes.c_int), ("width", ctypes.c_int), ("flags", ctypes.c_uint),
+                ("n", ctypes.c_int64), ("threshold", ctypes.c_int64), ("d_in", ctypes.c_void_p)]
+
+
+class cox_trace_item(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("req", cox_request)]
+
+
+class cox_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("max_batch", ctypes.c_int64), ("budget_bytes", ctypes.c_size_t),
+                ("used_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t), ("queued", ctypes.c_int64)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def make_request(kind: int, x, width: int = 32, compensated: bool = False, threshold: int = 0,
+                 unsigned: bool = False, n: int | None = None) -> cox_request:
+    """A cox_request over the CUDA tensor x (its first n elements)."""
+    t = _torch()
+    x = _dev_tensor(x)
+    if kind == COX_REQ_COMPACT:
+        dt = COX_U32 if unsigned else COX_I32
+    else:
+        dt = COX_F32 if x.dtype == t.float32 else COX_I32
+    return cox_request(kind, dt, width, COX_F_COMPENSATED if compensated else 0,
+                       x.numel() if n is None else int(n), int(threshold), x.data_ptr())
+
+
+class _DevView:
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 2}
+
+
+class Server:
+    """Continuous-batching request server (cox_server_*) over a device arena."""
+
+    def __init__(self, budget_bytes: int, max_requests: int = 1024):
+        self.handle = ctypes.c_void_p()
+        _check(lib().cox_server_create(int(budget_bytes), int(max_requests), ctypes.byref(self.handle)),
+               "cox_server_create")
+        self._keep = {}
+
+    def submit(self, req: cox_request, keep=None) -> int:
+        t = ctypes.c_uint64()
+        _check(lib().cox_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)), "cox_server_submit")
+        if keep is not None:
+            self._keep[t.value] = keep
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int()
+        _check(lib().cox_server_poll(self.handle, ticket, ctypes.byref(d)), "cox_server_poll")
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_s: float = 30.0) -> None:
+        _check(lib().cox_server_wait(self.handle, ticket, float(timeout_s)), "cox_server_wait")
+
+    def result(self, ticket: int, req: cox_request):
+        """A copy (torch CUDA tensor) of a done request's output."""
+        t = _torch()
+        p = ctypes.c_void_p()
+        c = ctypes.c_int64()
+        _check(lib().cox_server_result(self.handle, ticket, ctypes.byref(p), ctypes.byref(c)), "cox_server_result")
+        if req.kind == COX_REQ_REDUCE:
+            n, typ = 2, ("<f4" if req.dt == COX_F32 else "<i4")
+        else:
+            n, typ = c.value, ("<f4" if req.dt == COX_F32 else "<i4")
+        if n == 0:
+            return t.empty(0, dtype=t.float32 if typ == "<f4" else t.int32, device="cuda")
+        return t.as_tensor(_DevView(p.value, n, typ), device="cuda").clone()
+
+    def release(self, ticket: int) -> None:
+        _check(lib().cox_server_release(self.handle, ticket), "cox_server_release")
+        self._keep.pop(ticket, None)
+
+    def stats(self) -> dict:
+        st = cox_server_stats()
+        _check(lib().cox_server_get_stats(self.handle, ctypes.byref(st)), "cox_server_get_stats")
+        return st.asdict()
+
+    def run_trace(self, items):
+        """Replays (arrival_s, cox_request) pairs; returns (latencies list, wall seconds)."""
+        arr = (cox_trace_item * len(items))(*[cox_trace_item(a, r) for a, r in items])
+        lat = (ctypes.c_double * len(items))()
+        wall = ctypes.c_double()
+        _check(lib().cox_server_run_trace(self.handle, arr, len(items), lat, ctypes.byref(wall)),
+               "cox_server_run_trace")
+        return list(lat), wall.value
+
+    def close(self):
+        if self.handle:
+            lib().cox_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def percall_run_trace(items, scratch=None):
+    """The same trace with one launch per request (cox_percall_run_trace)."""
+    t = _torch()
+    max_n = max(r.n for _, r in items)
+    need = lib().cox_percall_scratch(max_n)
+    if scratch is None:
+        scratch = t.empty(need, dtype=t.uint8, device="cuda")
+    arr = (cox_trace_item * len(items))(*[cox_trace_item(a, r) for a, r in items])
+    lat = (ctypes.c_double * len(items))()
+    wall = ctypes.c_double()
+    _check(lib().cox_percall_run_trace(arr, len(items), scratch.data_ptr(), scratch.numel(), lat,
+                                       ctypes.byref(wall)), "cox_percall_run_trace")
+    return list(lat), wall.value

@@ -1,80 +1,11 @@
-// cox_ballot_compact: stable stream compaction from warp ballots.
-//
-// The filter of the SDK kernel filter_arr (Table 1 of the paper) with a
-// static, full-warp group instead of the dynamically coalesced one (the paper
-// covers non-divergent warp functions only, Section 2.2.3):
-//   b = __ballot_sync(full, key < t); rank = popc(b & lanemask_lt);
-// a shared-memory scan orders the warps of a tile, and tiles are ordered by
-// a single-pass decoupled look-back over per-tile descriptors.  Tiles are
-// handed out by an atomic ticket, so a tile only ever waits on tiles whose
-// CTAs already run: the waits end.  Each wait is still bounded.
-//
-// Tile layout: a CTA of B threads owns B*16 consecutive keys, read as four
-// 128-bit loads per thread; chunk j (4B keys) has thread t holding keys
-// j*4B + 4t .. 4t+3.  The rank of key (j, t, k) in the tile is
-//   offset(j, warp) + sum_k' popc(ballot_k'(j) & lanemask_lt) + #{k' < k kept}
-// which is its position in input order, so the result is the stable filter.
+// cox_ballot_compact: stable stream compaction from warp ballots (the tile
+// body lives in compact_tile.cuh).  One CTA per tile; tiles are handed out
+// by an atomic ticket in the order CTAs start.
 #include <mutex>
 
-#include "cox_common.cuh"
+#include "compact_tile.cuh"
 
 namespace cox {
-
-constexpr int kCompactEpt = 16;
-constexpr size_t kCompactWsHeader = 256;
-constexpr uint64_t kFlagA = 1ull << 62;  // descriptor holds the tile's own count
-constexpr uint64_t kFlagP = 2ull << 62;  // descriptor holds the inclusive prefix
-constexpr uint64_t kValMask = (1ull << 62) - 1;
-
-// Look-back by one warp: publish the tile's count, then walk predecessors 32
-// at a time until a published inclusive prefix is found.  Returns the
-// exclusive prefix of the tile (valid in every lane).
-__device__ __forceinline__ int64_t look_back(uint64_t* desc, int64_t tile, uint32_t total, uint32_t limit,
-                                             unsigned* status, bool& gave_up) {
-  const int lane = lane_id();
-  gave_up = false;
-  if (tile == 0) {
-    if (lane == 0) st_relaxed_u64(desc, kFlagP | total);
-    return 0;
-  }
-  if (lane == 0) st_relaxed_u64(desc + tile, kFlagA | total);
-  int64_t prefix = 0;
-  bool timed_out = false;
-  for (int64_t i = tile - 1 - lane;; i -= 32) {
-    uint64_t d = kFlagP;  // index < 0: the virtual predecessor of tile 0, prefix 0
-    if (i >= 0) {
-      d = ld_relaxed_u64(desc + i);
-      uint32_t polls = 0;
-      while ((d >> 62) == 0) {
-        if (++polls > limit) {
-          timed_out = true;
-          d = kFlagP;
-          break;
-        }
-        __nanosleep(200);
-        d = ld_relaxed_u64(desc + i);
-      }
-    }
-    const unsigned pmask = __ballot_sync(kFull, (d >> 62) == 2);
-    const int first = pmask ? __ffs(pmask) - 1 : 31;
-    unsigned long long v = lane <= first ? (d & kValMask) : 0ull;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-    prefix += (int64_t)v;
-    if (pmask) break;
-  }
-  if (__any_sync(kFull, timed_out)) {
-    gave_up = true;
-    prefix = 0;
-    if (lane == 0) {
-      atomicOr(status, (unsigned)kDevTimeout);
-      st_relaxed_u64(desc + tile, kFlagP);  // release successors with a zero prefix
-    }
-    return 0;
-  }
-  if (lane == 0) st_relaxed_u64(desc + tile, kFlagP | ((uint64_t)(prefix + total) & kValMask));
-  return prefix;
-}
 
 template <bool SIGNED>
 __global__ void __launch_bounds__(1024) k_ballot_compact(const uint32_t* __restrict__ keys, int64_t n,
@@ -83,104 +14,12 @@ __global__ void __launch_bounds__(1024) k_ballot_compact(const uint32_t* __restr
                                                          uint64_t* desc, int64_t ntiles, uint32_t limit,
                                                          unsigned* status, int vec) {
   extern __shared__ uint32_t smem[];
-  const int B = blockDim.x;
-  const int nw = B >> 5;
-  const int64_t TILE = (int64_t)B * kCompactEpt;
-  uint32_t* stage = smem;               // TILE words: the tile's kept keys, compacted
-  uint32_t* wcnt = smem + TILE;         // 4 * nw warp counts, then their offsets
-  __shared__ int64_t s_tile, s_prefix;
-  __shared__ uint32_t s_total;
-  __shared__ int s_gave_up;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+  __shared__ int64_t s_tile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);  // tiles in the order CTAs start
   __syncthreads();
   const int64_t tile = s_tile;
   if (tile >= ntiles) return;
-  const int64_t base = tile * TILE;
-
-  uint32_t key[4][4];
-  bool keep[4][4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int64_t e0 = base + (int64_t)j * 4 * B + 4 * tid;
-    if (vec && e0 + 4 <= n) {
-      const uint4 q = __ldcs(reinterpret_cast<const uint4*>(keys + e0));
-      key[j][0] = q.x; key[j][1] = q.y; key[j][2] = q.z; key[j][3] = q.w;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) keep[j][k] = true;
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        keep[j][k] = e0 + k < n;
-        key[j][k] = keep[j][k] ? keys[e0 + k] : 0u;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const bool p = SIGNED ? (int64_t)(int32_t)key[j][k] < thr : (int64_t)key[j][k] < thr;
-      keep[j][k] = keep[j][k] && p;
-    }
-  }
-  uint32_t lane_pre[4];
-  const unsigned lt = lanemask_lt();
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    uint32_t cnt = 0, pre = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const unsigned b = __ballot_sync(kFull, keep[j][k]);
-      cnt += __popc(b);
-      pre += __popc(b & lt);
-    }
-    lane_pre[j] = pre;
-    if (lane == 0) wcnt[j * nw + warp] = cnt;
-  }
-  __syncthreads();
-  if (warp == 0) {  // exclusive scan of the 4*nw warp counts in (chunk, warp) order
-    const int m = 4 * nw;
-    uint32_t c[4], sum = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int idx = lane * 4 + q;
-      c[q] = idx < m ? wcnt[idx] : 0u;
-      sum += c[q];
-    }
-    uint32_t incl = sum;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t u = __shfl_up_sync(kFull, incl, d);
-      if (lane >= d) incl += u;
-    }
-    uint32_t ex = incl - sum;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int idx = lane * 4 + q;
-      if (idx < m) wcnt[idx] = ex;
-      ex += c[q];
-    }
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    bool gave_up;
-    const int64_t prefix = look_back(desc, tile, total, limit, status, gave_up);
-    if (lane == 0) {
-      s_total = total;
-      s_prefix = prefix;
-      s_gave_up = gave_up;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    uint32_t o = wcnt[j * nw + warp] + lane_pre[j];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (keep[j][k]) stage[o++] = key[j][k];
-  }
-  __syncthreads();
-  const int64_t prefix = s_prefix;
-  const uint32_t total = s_total;
-  if (s_gave_up || prefix + (int64_t)total > n) return;
-  for (int i = tid; i < (int)total; i += B) out[prefix + i] = stage[i];
-  if (tile == ntiles - 1 && tid == 0) *d_count = prefix + total;
+  compact_tile<SIGNED>(keys, n, thr, out, d_count, desc, tile, ntiles, limit, status, vec, smem);
 }
 
 }  // namespace cox

@@ -137,6 +137,9 @@ struct Plain {
   __device__ static V shfl_down(V v, int d, int w) { return __shfl_down_sync(kFull, v, d, w); }
   __device__ static V shfl_up(V v, int d, int w) { return __shfl_up_sync(kFull, v, d, w); }
   __device__ static V shfl_idx(V v, int s, int w) { return __shfl_sync(kFull, v, s, w); }
+  // First step on freshly loaded values (nothing to carry): same as op/shfl_up.
+  __device__ static V shfl_up_fresh(V v, int d, int w) { return shfl_up(v, d, w); }
+  __device__ static V op_fresh(V a, V b) { return op(a, b); }
   __device__ static V redux32(V v) {
     if constexpr (kRedux) return Op::redux(v);
     else return v;
@@ -174,6 +177,15 @@ struct Comp {
   }
   __device__ static V shfl_idx(V v, int s, int w) {
     return {__shfl_sync(kFull, v.s, s, w), __shfl_sync(kFull, v.e, s, w)};
+  }
+  // First step on freshly loaded pairs, whose error words are all zero:
+  // only s moves, and (u, 0) (+) (s, 0) = (fl(u + s), (0 + 0) + t) = (., t)
+  // exactly, so the result equals op() bit for bit.
+  __device__ static V shfl_up_fresh(V v, int d, int w) { return {__shfl_up_sync(kFull, v.s, d, w), 0.0f}; }
+  __device__ static V op_fresh(V a, V b) {
+    V r;
+    two_sum(a.s, b.s, r.s, r.e);
+    return r;
   }
   __device__ static V redux32(V v) { return v; }
   __device__ static T out(V v) { return __fadd_rn(v.s, v.e); }
@@ -312,6 +324,46 @@ __device__ __forceinline__ void store_rows_tail(uint32_t* __restrict__ g, int64_
     const int64_t i = (int64_t)r * 32 + lane;
     if (i < avail) g[i] = row[r];
   }
+}
+
+// ------------------------------------------------------------ tile scan body
+// One warp chunk (ROWS x 32 elements starting at element c * ROWS * 32) of
+// the tile inclusive scan: Hillis-Steele steps d = 1, 2, .., W/2 of
+// u = shfl_up(x, d, W); if (rank >= d) x = u op x, ROWS independent rows.
+// `sm` is the warp's ROWS*32-word staging buffer; `vec` says whether full
+// chunks may use vector accesses (16-byte aligned in and out).
+template <class R, int W, int ROWS>
+__device__ __forceinline__ void scan_chunk(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,
+                                           int64_t c, uint32_t* sm, bool vec) {
+  using T = typename R::T;
+  using V = typename R::V;
+  constexpr int64_t CH = ROWS * 32;
+  const int rank = lane_id() & (W - 1);
+  const int64_t base = c * CH;
+  const bool full = vec && base + CH <= n;
+  uint32_t row[ROWS];
+  if (full) load_rows_full<ROWS>(in + base, sm, row);
+  else load_rows_tail<ROWS>(in + base, n - base, to_bits(R::pad()), row);
+  V v[ROWS];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) v[r] = R::load(from_bits<T>(row[r]));
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {  // d = 1 on fresh values
+    const V u = R::shfl_up_fresh(v[r], 1, W);
+    if (rank >= 1) v[r] = R::op_fresh(u, v[r]);
+  }
+#pragma unroll
+  for (int d = 2; d < W; d <<= 1) {
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      const V u = R::shfl_up(v[r], d, W);
+      if (rank >= d) v[r] = R::op(u, v[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) row[r] = to_bits(R::out(v[r]));
+  if (full) store_rows_full<ROWS>(out + base, sm, row);
+  else store_rows_tail<ROWS>(out + base, n - base, row);
 }
 
 // ------------------------------------------------- device status + waits

@@ -17,38 +17,13 @@ constexpr int kScanRows = 8;
 template <class R, int W, int ROWS>
 __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__ in,
                                                    uint32_t* __restrict__ out, int64_t n, int vec) {
-  using T = typename R::T;
-  using V = typename R::V;
   extern __shared__ uint32_t smem[];
   uint32_t* sm = smem + (threadIdx.x >> 5) * (ROWS * 32);
   constexpr int64_t CH = ROWS * 32;
   const int64_t nchunks = (n + CH - 1) / CH;
-  const int64_t nfull = vec ? n / CH : 0;
-  const int rank = lane_id() & (W - 1);
   const int64_t wpb = blockDim.x >> 5;
-  const uint32_t pad = to_bits(R::pad());
-  for (int64_t c = blockIdx.x * wpb + (threadIdx.x >> 5); c < nchunks; c += gridDim.x * wpb) {
-    const int64_t base = c * CH;
-    const bool full = c < nfull;
-    uint32_t row[ROWS];
-    if (full) load_rows_full<ROWS>(in + base, sm, row);
-    else load_rows_tail<ROWS>(in + base, n - base, pad, row);
-    V v[ROWS];
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r) v[r] = R::load(from_bits<T>(row[r]));
-#pragma unroll
-    for (int d = 1; d < W; d <<= 1) {
-#pragma unroll
-      for (int r = 0; r < ROWS; ++r) {
-        const V u = R::shfl_up(v[r], d, W);
-        if (rank >= d) v[r] = R::op(u, v[r]);
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r) row[r] = to_bits(R::out(v[r]));
-    if (full) store_rows_full<ROWS>(out + base, sm, row);
-    else store_rows_tail<ROWS>(out + base, n - base, row);
-  }
+  for (int64_t c = blockIdx.x * wpb + (threadIdx.x >> 5); c < nchunks; c += gridDim.x * wpb)
+    scan_chunk<R, W, ROWS>(in, out, n, c, sm, vec != 0);
 }
 
 template <class R, int W>

@@ -1,0 +1,723 @@
+// Request server: continuous batching of reduce, scan and compact requests.
+//
+// Host side.  A device arena of `budget` bytes holds every admitted
+// request's output and workspace; a scheduler thread admits queued requests
+// in arrival order while the arena and the slot count allow, packs all
+// admitted, not yet launched requests into one persistent launch on one of
+// kSlots streams (so a batch launched while an earlier one runs overlaps it
+// on the device), and marks requests done when their batch's event fires.
+//
+// Device side.  A batch is a table of request descriptors; each request is
+// cut into tiles of kTile elements, numbered consecutively request by
+// request.  Persistent CTAs take tile numbers from an atomic counter, so a
+// request's tiles are taken in order: a compaction tile only ever waits (in
+// its look-back) on smaller tiles of its own request, already taken by CTAs
+// that run.  Per tile:
+//   REDUCE  fold 16 elements per thread (TwoSum pairs for fp32), block tree,
+//           partial to the workspace; the request's last tile folds all
+//           partials in tile order.
+//   SCAN    the tile scan (scan_chunk) on 16 warp chunks of 256 elements.
+//   COMPACT the compaction tile (compact_tile), look-back over the
+//           request's own descriptors.
+// A request's arithmetic depends only on the request, never on its batch.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "compact_tile.cuh"
+
+namespace cox {
+
+constexpr int kServeBlock = 256;
+constexpr int64_t kTile = kServeBlock * 16;  // 4096 elements, the compaction tile at 256 threads
+constexpr int kSlots = 3;                    // batches in flight
+constexpr int kMaxBatch = 2048;              // requests per launch
+constexpr size_t kAlign = 256;
+
+struct ReqDesc {
+  int kind, dt, width;
+  unsigned flags;
+  int64_t n, threshold;
+  const uint32_t* in;
+  uint32_t* out;
+  uint8_t* ws;
+  int64_t item0, nitems;
+};
+
+struct BatchHdr {
+  unsigned long long next;
+  int64_t nitems;
+  int nreq;
+  int pad[11];
+};  // 64 bytes, followed by nreq ReqDesc
+static_assert(sizeof(BatchHdr) == 64, "batch header layout");
+
+__host__ __device__ inline int64_t serve_items(int64_t n) { return (n + kTile - 1) / kTile; }
+
+// Dynamic shared memory of k_serve: the compaction tile (kTile + 4 words per
+// warp, reused by scan staging) plus the per-request first-tile table.
+inline size_t serve_smem(size_t nreq) { return (size_t)(kTile + 4 * (kServeBlock / 32) + nreq) * 4; }
+
+// ---------------------------------------------------------------- reduce
+template <class R>
+__device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, typename R::V* wpart) {
+  using T = typename R::T;
+  using V = typename R::V;
+  const int tid = threadIdx.x;
+  const int64_t base = c * kTile;
+  const bool vec = (reinterpret_cast<uintptr_t>(d.in) & 15u) == 0;
+  V acc = R::ident();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int64_t e0 = base + (int64_t)j * 4 * kServeBlock + 4 * tid;
+    if (vec && e0 + 4 <= d.n) {
+      const uint4 q = __ldcs(reinterpret_cast<const uint4*>(d.in + e0));
+      acc = R::op(acc, R::load(from_bits<T>(q.x)));
+      acc = R::op(acc, R::load(from_bits<T>(q.y)));
+      acc = R::op(acc, R::load(from_bits<T>(q.z)));
+      acc = R::op(acc, R::load(from_bits<T>(q.w)));
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (e0 + k < d.n) acc = R::op(acc, R::load(from_bits<T>(d.in[e0 + k])));
+    }
+  }
+  const V bsum = block_reduce32<R>(acc, wpart);
+  unsigned* ctr = reinterpret_cast<unsigned*>(d.ws);
+  V* part = reinterpret_cast<V*>(d.ws + kAlign);
+  __shared__ int s_last;
+  if (tid == 0) {
+    part[c] = bsum;
+    __threadfence();
+    s_last = atomicAdd(ctr, 1u) == (unsigned)(d.nitems - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  V fold = R::ident();
+  for (int64_t k = tid; k < d.nitems; k += kServeBlock) {
+    V pv;
+    if constexpr (R::kComp) {
+      const float2 f = __ldcg(reinterpret_cast<const float2*>(part) + k);
+      pv = {f.x, f.y};
+    } else {
+      pv = from_bits<T>(__ldcg(reinterpret_cast<const uint32_t*>(part) + k));
+    }
+    fold = R::op(fold, pv);
+  }
+  const V total = block_reduce32<R>(fold, wpart);
+  if (tid == 0) {
+    d.out[0] = to_bits(R::out(total));
+    d.out[1] = __float_as_uint(R::lo(total));
+  }
+}
+
+// ------------------------------------------------------------------ scan
+template <class R, int W>
+__device__ void serve_scan_tile_w(const ReqDesc& d, int64_t c, uint32_t* smem) {
+  const int warp = threadIdx.x >> 5;
+  uint32_t* sm = smem + warp * 256;
+  const bool vec = ((reinterpret_cast<uintptr_t>(d.in) | reinterpret_cast<uintptr_t>(d.out)) & 15u) == 0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t chunk = c * (kTile / 256) + warp * 2 + h;
+    if (chunk * 256 < d.n) scan_chunk<R, W, 8>(d.in, d.out, d.n, chunk, sm, vec);
+  }
+}
+
+template <class R>
+__device__ void serve_scan_tile(const ReqDesc& d, int64_t c, uint32_t* smem) {
+  switch (d.width) {
+    case 2: serve_scan_tile_w<R, 2>(d, c, smem); break;
+    case 4: serve_scan_tile_w<R, 4>(d, c, smem); break;
+    case 8: serve_scan_tile_w<R, 8>(d, c, smem); break;
+    case 16: serve_scan_tile_w<R, 16>(d, c, smem); break;
+    default: serve_scan_tile_w<R, 32>(d, c, smem); break;
+  }
+}
+
+__global__ void __launch_bounds__(kServeBlock, 4) k_serve(uint8_t* table, uint32_t limit, unsigned* status) {
+  extern __shared__ uint32_t smem[];
+  __shared__ Pair wpart_c[32];
+  __shared__ uint32_t wpart_u[32];
+  __shared__ float wpart_f[32];
+  __shared__ int64_t s_item;
+  __shared__ int s_req;
+  BatchHdr* hdr = reinterpret_cast<BatchHdr*>(table);
+  const ReqDesc* reqs = reinterpret_cast<const ReqDesc*>(table + sizeof(BatchHdr));
+  const int64_t nitems = hdr->nitems;
+  const int nreq = hdr->nreq;
+  // First tile of every request, staged once per CTA so that finding a tile's
+  // request is a binary search in shared memory (tile numbers fit 32 bits:
+  // a batch holds at most kMaxBatch requests of < 2^31 tiles in total).
+  uint32_t* first = smem + kTile + 4 * (kServeBlock / 32);
+  for (int r = threadIdx.x; r < nreq; r += blockDim.x) first[r] = (uint32_t)reqs[r].item0;
+  for (;;) {
+    __syncthreads();  // the previous tile is done with shared memory
+    if (threadIdx.x == 0) {
+      const int64_t item = (int64_t)atomicAdd(&hdr->next, 1ull);
+      s_item = item;
+      if (item < nitems) {
+        int lo = 0, hi = nreq;  // last request whose first tile <= item
+        while (hi - lo > 1) {
+          const int m = (lo + hi) >> 1;
+          if ((int64_t)first[m] <= item) lo = m;
+          else hi = m;
+        }
+        s_req = lo;
+      }
+    }
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= nitems) return;
+    const ReqDesc d = reqs[s_req];
+    const int64_t c = item - d.item0;
+    if (d.kind == COX_REQ_REDUCE) {
+      if (d.dt == COX_F32) {
+        if (d.flags & COX_F_COMPENSATED) serve_reduce_tile<Comp>(d, c, wpart_c);
+        else serve_reduce_tile<Plain<AddF>>(d, c, wpart_f);
+      } else {
+        serve_reduce_tile<Plain<AddU>>(d, c, wpart_u);
+      }
+    } else if (d.kind == COX_REQ_SCAN) {
+      if (d.dt == COX_F32) {
+        if (d.flags & COX_F_COMPENSATED) serve_scan_tile<Comp>(d, c, smem);
+        else serve_scan_tile<Plain<AddF>>(d, c, smem);
+      } else {
+        serve_scan_tile<Plain<AddU>>(d, c, smem);
+      }
+    } else {
+      int64_t* count = reinterpret_cast<int64_t*>(d.ws);
+      uint64_t* desc = reinterpret_cast<uint64_t*>(d.ws + kAlign);
+      const int vec = (reinterpret_cast<uintptr_t>(d.in) & 15u) == 0;
+      if (d.dt == COX_I32)
+        compact_tile<true>(d.in, d.n, d.threshold, d.out, count, desc, c, d.nitems, limit, status, vec, smem);
+      else
+        compact_tile<false>(d.in, d.n, d.threshold, d.out, count, desc, c, d.nitems, limit, status, vec, smem);
+    }
+  }
+}
+
+// Zeroes what each request's tiles expect at zero: the reduce counter, the
+// compaction count and look-back descriptors.
+__global__ void k_serve_prep(const uint8_t* __restrict__ table) {
+  const BatchHdr* hdr = reinterpret_cast<const BatchHdr*>(table);
+  const ReqDesc* reqs = reinterpret_cast<const ReqDesc*>(table + sizeof(BatchHdr));
+  if ((int)blockIdx.x >= hdr->nreq) return;
+  const ReqDesc d = reqs[blockIdx.x];
+  if (d.kind == COX_REQ_SCAN) return;
+  const size_t words = d.kind == COX_REQ_COMPACT ? (kAlign + (size_t)d.nitems * 8) / 4 : kAlign / 4;
+  uint32_t* w = reinterpret_cast<uint32_t*>(d.ws);
+  for (size_t i = threadIdx.x; i < words; i += blockDim.x) w[i] = 0u;
+}
+
+// --------------------------------------------------------------- host side
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+size_t round_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+// Bytes a request holds in the arena: [output | workspace].
+void request_bytes(const cox_request& r, size_t* out_b, size_t* ws_b) {
+  const int64_t items = serve_items(r.n);
+  switch (r.kind) {
+    case COX_REQ_REDUCE: *out_b = kAlign; *ws_b = kAlign + round_up((size_t)items * 8); break;
+    case COX_REQ_SCAN: *out_b = round_up((size_t)r.n * 4); *ws_b = 0; break;
+    default: *out_b = round_up((size_t)r.n * 4); *ws_b = kAlign + round_up((size_t)items * 8); break;
+  }
+}
+
+cox_status check_request(const cox_request& r) {
+  if (!r.d_in || r.n < 1) return COX_EINVAL;
+  if (r.n >= (int64_t(1) << 31)) return COX_EUNSUPPORTED;  // keeps a batch's tile numbers below 2^31
+  switch (r.kind) {
+    case COX_REQ_REDUCE:
+    case COX_REQ_SCAN:
+      if (r.dt != COX_F32 && r.dt != COX_I32) return COX_EINVAL;
+      if ((r.flags & COX_F_COMPENSATED) && r.dt != COX_F32) return COX_EINVAL;
+      if (r.flags & ~(unsigned)COX_F_COMPENSATED) return COX_EINVAL;
+      if (r.kind == COX_REQ_SCAN && !valid_width(r.width)) return COX_EINVAL;
+      return COX_OK;
+    case COX_REQ_COMPACT:
+      return (r.dt == COX_I32 || r.dt == COX_U32) ? COX_OK : COX_EINVAL;
+    default:
+      return COX_EINVAL;
+  }
+}
+
+// First-fit allocator over [0, cap) with coalescing; sizes are multiples of kAlign.
+class Arena {
+ public:
+  explicit Arena(size_t cap) : cap_(cap) { free_[0] = cap; }
+  bool alloc(size_t bytes, size_t* off) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes;
+        const size_t at = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[at] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    auto next = free_.lower_bound(off);
+    if (next != free_.end() && off + bytes == next->first) {
+      bytes += next->second;
+      next = free_.erase(next);
+    }
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == off) {
+        prev->second += bytes;
+        return;
+      }
+    }
+    free_[off] = bytes;
+  }
+
+ private:
+  size_t cap_;
+  std::map<size_t, size_t> free_;
+};
+
+enum ReqState { kQueued, kReady, kRunning, kDone, kFailed };
+
+struct SReq {
+  cox_request r;
+  ReqState state = kQueued;
+  size_t off = 0, bytes = 0, out_b = 0, held = 0;
+  double t_done = 0.0;
+};
+
+struct Slot {
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  uint8_t* host_tab = nullptr;
+  uint8_t* dev_tab = nullptr;
+  bool busy = false;
+  std::vector<uint64_t> tickets;
+};
+
+}  // namespace cox
+
+using namespace cox;
+
+struct cox_server {
+  int dev = 0;
+  uint8_t* arena_mem = nullptr;
+  size_t budget = 0;
+  Arena* arena = nullptr;
+  size_t used = 0, peak = 0;
+  int max_req = 0;
+  int admitted = 0;
+  int grid = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<uint64_t> queue;
+  std::vector<uint64_t> ready;
+  std::unordered_map<uint64_t, SReq> reqs;
+  std::vector<std::pair<uint64_t, double>> finished;  // (ticket, t_done) for trace runners
+  bool collect_finished = false;
+  Slot slots[kSlots];
+  std::thread thr;
+  std::atomic<bool> stop{false};
+  uint64_t next_ticket = 1;
+  cox_server_stats stats{};
+
+  void launch_batch(Slot& sl, const std::vector<uint64_t>& ts) {
+    BatchHdr* h = reinterpret_cast<BatchHdr*>(sl.host_tab);
+    ReqDesc* d = reinterpret_cast<ReqDesc*>(sl.host_tab + sizeof(BatchHdr));
+    int64_t items = 0;
+    for (size_t i = 0; i < ts.size(); ++i) {
+      SReq& q = reqs[ts[i]];
+      ReqDesc& e = d[i];
+      e.kind = q.r.kind;
+      e.dt = q.r.dt;
+      e.width = q.r.width;
+      e.flags = q.r.flags;
+      e.n = q.r.n;
+      e.threshold = q.r.threshold;
+      e.in = static_cast<const uint32_t*>(q.r.d_in);
+      e.out = reinterpret_cast<uint32_t*>(arena_mem + q.off);
+      e.ws = arena_mem + q.off + q.out_b;
+      e.item0 = items;
+      e.nitems = serve_items(q.r.n);
+      items += e.nitems;
+      q.state = kRunning;
+    }
+    // (requests are < 2^31 elements each, so 2048 of them stay < 2^31 tiles)
+    h->next = 0;
+    h->nitems = items;
+    h->nreq = (int)ts.size();
+    const size_t tab_bytes = sizeof(BatchHdr) + ts.size() * sizeof(ReqDesc);
+    bool ok = cudaMemcpyAsync(sl.dev_tab, sl.host_tab, tab_bytes, cudaMemcpyHostToDevice, sl.st) == cudaSuccess;
+    if (ok) {
+      k_serve_prep<<<(unsigned)ts.size(), 256, 0, sl.st>>>(sl.dev_tab);
+      const int g = (int)std::min<int64_t>(grid, items);
+      const size_t smem = serve_smem(ts.size());
+      k_serve<<<g, kServeBlock, smem, sl.st>>>(sl.dev_tab, spin_limit(), device_status_word());
+      ok = cudaGetLastError() == cudaSuccess && cudaEventRecord(sl.ev, sl.st) == cudaSuccess;
+    }
+    sl.tickets = ts;
+    sl.busy = true;
+    stats.batches += 1;
+    stats.max_batch = std::max<int64_t>(stats.max_batch, (int64_t)ts.size());
+    if (!ok) {  // the batch's requests fail; the event query below reports them
+      for (uint64_t t : ts) reqs[t].state = kFailed;
+      sl.busy = false;
+      stats.failed += (int64_t)ts.size();
+      cv.notify_all();
+    }
+  }
+
+  void loop() {
+    cudaSetDevice(dev);
+    while (!stop.load(std::memory_order_relaxed)) {
+      bool progress = false;
+      {
+        std::lock_guard<std::mutex> g(mu);
+        for (Slot& sl : slots) {  // completions
+          if (!sl.busy) continue;
+          const cudaError_t e = cudaEventQuery(sl.ev);
+          if (e == cudaErrorNotReady) continue;
+          const double t = now_s();
+          for (uint64_t tk : sl.tickets) {
+            auto it = reqs.find(tk);
+            if (it == reqs.end()) continue;
+            it->second.state = e == cudaSuccess ? kDone : kFailed;
+            it->second.t_done = t;
+            if (collect_finished) finished.emplace_back(tk, t);
+          }
+          if (e == cudaSuccess) stats.completed += (int64_t)sl.tickets.size();
+          else stats.failed += (int64_t)sl.tickets.size();
+          sl.busy = false;
+          sl.tickets.clear();
+          progress = true;
+          cv.notify_all();
+        }
+        while (!queue.empty() && admitted < max_req) {  // admission, in arrival order
+          SReq& q = reqs[queue.front()];
+          size_t off;
+          if (used + q.held > budget || !arena->alloc(q.bytes, &off)) break;
+          q.off = off;
+          q.state = kReady;
+          used += q.held;
+          peak = std::max(peak, used);
+          ++admitted;
+          ready.push_back(queue.front());
+          queue.pop_front();
+          progress = true;
+        }
+        if (!ready.empty()) {  // launch everything admitted on a free stream
+          for (Slot& sl : slots) {
+            if (sl.busy) continue;
+            const size_t k = std::min<size_t>(ready.size(), kMaxBatch);
+            std::vector<uint64_t> ts(ready.begin(), ready.begin() + k);
+            ready.erase(ready.begin(), ready.begin() + k);
+            launch_batch(sl, ts);
+            progress = true;
+            break;
+          }
+        }
+      }
+      if (!progress) std::this_thread::yield();
+    }
+  }
+};
+
+extern "C" cox_status cox_server_create(size_t budget_bytes, int max_requests, cox_server** out) {
+  if (!out || budget_bytes < kAlign || max_requests < 1) return COX_EINVAL;
+  *out = nullptr;
+  cox_server* s = new (std::nothrow) cox_server;
+  if (!s) return COX_ENOMEM;
+  if (cudaGetDevice(&s->dev) != cudaSuccess) {
+    delete s;
+    return COX_ECUDA;
+  }
+  s->budget = budget_bytes & ~(kAlign - 1);
+  s->max_req = max_requests;
+  if (cudaMalloc(&s->arena_mem, s->budget) != cudaSuccess) {
+    delete s;
+    return COX_ENOMEM;
+  }
+  s->arena = new Arena(s->budget);
+  const size_t tab = sizeof(BatchHdr) + (size_t)kMaxBatch * sizeof(ReqDesc);
+  for (Slot& sl : s->slots) {
+    if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost(&sl.host_tab, tab) != cudaSuccess || cudaMalloc(&sl.dev_tab, tab) != cudaSuccess) {
+      cox_server_destroy(s);
+      return COX_ECUDA;
+    }
+  }
+  const size_t smem = serve_smem(kMaxBatch);
+  if (cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cox_server_destroy(s);
+    return COX_ECUDA;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve, kServeBlock, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  s->grid = per_sm * sm_count();
+  device_status_word();
+  s->stats.budget_bytes = s->budget;
+  s->thr = std::thread([s] { s->loop(); });
+  *out = s;
+  return COX_OK;
+}
+
+extern "C" cox_status cox_server_submit(cox_server* s, const cox_request* req, uint64_t* ticket) {
+  if (!s || !req || !ticket) return COX_EINVAL;
+  const cox_status c = check_request(*req);
+  if (c != COX_OK) return c;
+  SReq q;
+  q.r = *req;
+  size_t ob, wb;
+  request_bytes(*req, &ob, &wb);
+  q.out_b = ob;
+  q.bytes = ob + wb;
+  q.held = q.bytes + round_up((size_t)req->n * 4);  // input counted as held while in flight
+  if (q.bytes > s->budget || q.held > s->budget) return COX_ENOMEM;
+  std::lock_guard<std::mutex> g(s->mu);
+  const uint64_t t = s->next_ticket++;
+  s->reqs.emplace(t, q);
+  s->queue.push_back(t);
+  s->stats.submitted += 1;
+  *ticket = t;
+  return COX_OK;
+}
+
+extern "C" cox_status cox_server_poll(cox_server* s, uint64_t ticket, int* done) {
+  if (!s || !done) return COX_EINVAL;
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return COX_EINVAL;
+  if (it->second.state == kFailed) return COX_ECUDA;
+  *done = it->second.state == kDone;
+  return COX_OK;
+}
+
+extern "C" cox_status cox_server_wait(cox_server* s, uint64_t ticket, double timeout_s) {
+  if (!s) return COX_EINVAL;
+  std::unique_lock<std::mutex> g(s->mu);
+  auto pred = [&] {
+    auto it = s->reqs.find(ticket);
+    return it == s->reqs.end() || it->second.state == kDone || it->second.state == kFailed;
+  };
+  if (!s->cv.wait_for(g, std::chrono::duration<double>(timeout_s), pred)) return COX_ETIMEOUT;
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return COX_EINVAL;
+  return it->second.state == kDone ? COX_OK : COX_ECUDA;
+}
+
+extern "C" cox_status cox_server_result(cox_server* s, uint64_t ticket, void** d_out, int64_t* count) {
+  if (!s || !d_out || !count) return COX_EINVAL;
+  cox_request r;
+  uint8_t* out;
+  size_t out_b;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end() || it->second.state != kDone) return COX_EINVAL;
+    r = it->second.r;
+    out = s->arena_mem + it->second.off;
+    out_b = it->second.out_b;
+  }
+  *d_out = out;
+  if (r.kind == COX_REQ_REDUCE) *count = 1;
+  else if (r.kind == COX_REQ_SCAN) *count = r.n;
+  else if (cudaMemcpy(count, out + out_b, sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess) return COX_ECUDA;
+  return COX_OK;
+}
+
+static void release_locked(cox_server* s, std::unordered_map<uint64_t, SReq>::iterator it) {
+  s->arena->release(it->second.off, it->second.bytes);
+  s->used -= it->second.held;
+  s->admitted -= 1;
+  s->reqs.erase(it);
+}
+
+extern "C" cox_status cox_server_release(cox_server* s, uint64_t ticket) {
+  if (!s) return COX_EINVAL;
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return COX_EINVAL;
+  if (it->second.state != kDone && it->second.state != kFailed) return COX_EBUSY;
+  release_locked(s, it);
+  return COX_OK;
+}
+
+extern "C" cox_status cox_server_get_stats(cox_server* s, cox_server_stats* st) {
+  if (!s || !st) return COX_EINVAL;
+  std::lock_guard<std::mutex> g(s->mu);
+  *st = s->stats;
+  st->used_bytes = s->used;
+  st->peak_bytes = s->peak;
+  st->queued = (int64_t)s->queue.size();
+  return COX_OK;
+}
+
+extern "C" void cox_server_destroy(cox_server* s) {
+  if (!s) return;
+  if (s->thr.joinable()) {
+    for (;;) {  // let launched batches finish
+      bool busy = false;
+      {
+        std::lock_guard<std::mutex> g(s->mu);
+        for (Slot& sl : s->slots) busy = busy || sl.busy;
+      }
+      if (!busy) break;
+      std::this_thread::yield();
+    }
+    s->stop.store(true);
+    s->thr.join();
+  }
+  for (Slot& sl : s->slots) {
+    if (sl.st) cudaStreamSynchronize(sl.st);
+    if (sl.ev) cudaEventDestroy(sl.ev);
+    if (sl.st) cudaStreamDestroy(sl.st);
+    if (sl.host_tab) cudaFreeHost(sl.host_tab);
+    if (sl.dev_tab) cudaFree(sl.dev_tab);
+  }
+  if (s->arena_mem) cudaFree(s->arena_mem);
+  delete s->arena;
+  delete s;
+}
+
+// ------------------------------------------------------------ trace runners
+extern "C" cox_status cox_server_run_trace(cox_server* s, const cox_trace_item* items, int64_t count,
+                                           double* latency_s, double* wall_s) {
+  if (!s || (count > 0 && (!items || !latency_s)) || !wall_s) return COX_EINVAL;
+  std::unordered_map<uint64_t, int64_t> index;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->finished.clear();
+    s->collect_finished = true;
+  }
+  const double t0 = now_s();
+  int64_t next = 0, done = 0;
+  cox_status rc = COX_OK;
+  std::vector<std::pair<uint64_t, double>> fin;
+  double last = t0;
+  while (done < count) {
+    const double t = now_s() - t0;
+    while (next < count && items[next].arrival_s <= t) {
+      uint64_t tk;
+      const cox_status c = cox_server_submit(s, &items[next].req, &tk);
+      if (c != COX_OK) {
+        rc = c;
+        latency_s[next] = -1.0;
+        ++done;
+      } else {
+        index[tk] = next;
+      }
+      ++next;
+    }
+    {
+      std::lock_guard<std::mutex> g(s->mu);
+      fin.swap(s->finished);
+    }
+    for (auto& f : fin) {
+      auto it = index.find(f.first);
+      if (it == index.end()) continue;
+      latency_s[it->second] = f.second - (t0 + items[it->second].arrival_s);
+      last = std::max(last, f.second);
+      cox_server_release(s, f.first);
+      index.erase(it);
+      ++done;
+    }
+    fin.clear();
+    if (fin.empty() && next < count) std::this_thread::yield();
+  }
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->collect_finished = false;
+    s->finished.clear();
+  }
+  *wall_s = last - t0;
+  return rc;
+}
+
+extern "C" size_t cox_percall_scratch(int64_t max_n) {
+  if (max_n < 1) return 0;
+  return round_up(cox_tile_reduce_workspace(COX_SCOPE_GRID, max_n, 256)) +
+         round_up(cox_ballot_compact_workspace(max_n, 256)) + kAlign + round_up((size_t)max_n * 4);
+}
+
+extern "C" cox_status cox_percall_run_trace(const cox_trace_item* items, int64_t count, void* d_scratch,
+                                            size_t scratch_bytes, double* latency_s, double* wall_s) {
+  if ((count > 0 && (!items || !latency_s)) || !wall_s || !d_scratch) return COX_EINVAL;
+  int64_t max_n = 1;
+  for (int64_t i = 0; i < count; ++i) max_n = std::max(max_n, items[i].req.n);
+  if (scratch_bytes < cox_percall_scratch(max_n)) return COX_ENOMEM;
+  uint8_t* p = static_cast<uint8_t*>(d_scratch);
+  const size_t red_b = round_up(cox_tile_reduce_workspace(COX_SCOPE_GRID, max_n, 256));
+  const size_t cmp_b = round_up(cox_ballot_compact_workspace(max_n, 256));
+  uint8_t* red_ws = p;
+  uint8_t* cmp_ws = p + red_b;
+  int64_t* d_count = reinterpret_cast<int64_t*>(p + red_b + cmp_b);
+  uint8_t* out = p + red_b + cmp_b + kAlign;
+  cudaStream_t st;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return COX_ECUDA;
+  std::vector<cudaEvent_t> ev((size_t)count, nullptr);
+  for (auto& e : ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return COX_ECUDA;
+  std::vector<std::atomic<int>> launched((size_t)count);
+  for (auto& l : launched) l.store(0);
+  std::vector<double> t_done((size_t)count, 0.0);
+  std::atomic<bool> failed{false};
+  std::thread poller([&] {
+    for (int64_t i = 0; i < count; ++i) {
+      while (!launched[i].load(std::memory_order_acquire)) std::this_thread::yield();
+      if (launched[i].load() < 0) continue;
+      cudaError_t e;
+      while ((e = cudaEventQuery(ev[i])) == cudaErrorNotReady) std::this_thread::yield();
+      if (e != cudaSuccess) failed.store(true);
+      t_done[i] = now_s();
+    }
+  });
+  const double t0 = now_s();
+  cox_status rc = COX_OK;
+  for (int64_t i = 0; i < count; ++i) {
+    while (now_s() - t0 < items[i].arrival_s) {
+    }
+    const cox_request& r = items[i].req;
+    cox_status c = check_request(r);
+    if (c == COX_OK) {
+      if (r.kind == COX_REQ_REDUCE)
+        c = cox_tile_reduce(COX_SUM, r.dt, 32, 256, COX_SCOPE_GRID, r.d_in, out, r.n, r.flags, out + 4, red_ws,
+                            red_b, st);
+      else if (r.kind == COX_REQ_SCAN)
+        c = cox_tile_scan(COX_SUM, r.dt, r.width, 256, r.d_in, out, r.n, r.flags, st);
+      else
+        c = cox_ballot_compact(r.dt, 32, 256, r.d_in, r.n, r.threshold, out, d_count, cmp_ws, cmp_b, 0, st);
+    }
+    if (c == COX_OK && cudaEventRecord(ev[i], st) != cudaSuccess) c = COX_ECUDA;
+    if (c != COX_OK) rc = c;
+    launched[i].store(c == COX_OK ? 1 : -1, std::memory_order_release);
+  }
+  poller.join();
+  double last = t0;
+  for (int64_t i = 0; i < count; ++i) {
+    latency_s[i] = launched[i].load() > 0 ? t_done[i] - (t0 + items[i].arrival_s) : -1.0;
+    last = std::max(last, t_done[i]);
+  }
+  *wall_s = last - t0;
+  for (auto& e : ev) cudaEventDestroy(e);
+  cudaStreamDestroy(st);
+  if (failed.load()) return COX_ECUDA;
+  return rc;
+}
