@@ -164,8 +164,9 @@ cox_status cox_tile_scan(cox_op op, cox_dtype dt, int width, int block_dim, cons
  *   unless flags has COX_F_WS_READY, in which case the caller guarantees those
  *   bytes are zero.  Not shared across concurrent calls.
  *   flags: 0 or COX_F_WS_READY.
- * Tiles of block_dim * 16 keys are ordered by a ticket counter; each tile's
- * look-back polls its predecessors' descriptors.  A poll that exceeds the spin
+ * Tiles of 16384 keys (one CTA of block_dim threads each; block_dim only
+ * shapes the launch) are ordered by a ticket counter; each tile's look-back
+ * polls its predecessors' descriptors.  A poll that exceeds the spin
  * limit (cox_set_spin_limit) gives up: the tile publishes a zero prefix, writes
  * nothing, and COX_ETIMEOUT is recorded for cox_device_status().  Every write
  * stays inside d_out[0, n) and d_count.
@@ -189,8 +190,8 @@ size_t cox_ballot_compact_workspace(int64_t n, int block_dim);
  * flags.  The scratch is a fixed array of COX_COMPACT_STATIC_SCRATCH_BYTES
  * (1 MiB) inside libcox.so, held on every GPU that loads the library until
  * the process exits.  It fits 256 bytes of header plus 8 bytes per tile of
- * block_dim * 16 keys: n <= 131040 * block_dim * 16 (536,739,840 keys at
- * block_dim 256).  Larger n returns COX_ENOMEM before anything is enqueued.
+ * 16384 keys: n <= 131040 * 16384 (2,146,959,360 keys).  Larger n returns
+ * COX_ENOMEM before anything is enqueued.
  * The call allocates nothing (no cudaMalloc/cudaFree) and clears the scratch
  * bytes it uses with a cudaMemsetAsync on `stream` before its kernel.
  * The first call on a device looks up the array's device address (with that

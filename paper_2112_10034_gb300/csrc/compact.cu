@@ -1,11 +1,122 @@
-// cox_ballot_compact: stable stream compaction from warp ballots (the tile
-// body lives in compact_tile.cuh).  One CTA per tile; tiles are handed out
-// by an atomic ticket in the order CTAs start.
+// cox_ballot_compact: stable stream compaction from warp ballots.
+//
+// One CTA per tile of 16384 keys (64 KB), taken from an atomic ticket in the
+// order CTAs start; the CTA's B threads cover the tile in 16384 / (16 B)
+// passes of 16 keys each (4 passes at B = 256, 1 at B = 1024).  The tile arrives in shared memory by one
+// TMA bulk copy (plain loads for a ragged or unaligned tile), so keys never
+// occupy registers and three 64 KB tiles fit in flight per SM -- a tile's
+// chain of round trips (ticket, copy, look-back) is what bounds this op, and
+// only bytes in flight hide it.  In the tile:
+//   count   per pass, 16 keys per thread, each warp on its own run of 512
+//           keys: lanes count kept keys (key < t), redux.sync sums the
+//           warp's count (32 counts per tile whatever B);
+//   scan    warp 0 scans the counts in (pass, warp) order and publishes the
+//           tile's count for the look-back;
+//   compact the same passes again: per chunk of the run, b = __ballot_sync
+//           (keep) for each of a lane's four key slots, rank = offset +
+//           earlier chunks + popc(b & lanemask_lt) + kept keys before it in
+//           the lane; kept keys move in place to their rank (a key's rank
+//           never exceeds its own index, and pass j only writes below
+//           16B(j+1), where pass j+1 reads, so one barrier per pass between
+//           its reads and writes suffices);
+//   prefix  warp 0's decoupled look-back (compact_tile.cuh);
+//   out     coalesced copy of the compacted keys to out[prefix ..].
+// Each CTA's ticket is taken as it starts and its tile finished before it
+// exits, so every look-back wait ends; each is bounded all the same.
 #include <mutex>
 
 #include "compact_tile.cuh"
 
 namespace cox {
+
+constexpr int64_t kBigTile = 16384;  // keys per tile (64 KB); 16 * block_dim divides it for every block_dim
+
+// key < thr as one 32-bit compare: thr is clamped into the key range first
+// (every key passes if thr is above the range, none if at or below it).
+struct KeepRule {
+  uint32_t t;  // keep iff key < t in the key's own signedness...
+  int mode;    // ...when mode == 0; mode 1 keeps all, mode 2 keeps none
+};
+
+template <bool SIGNED>
+__host__ __device__ inline KeepRule keep_rule(int64_t thr) {
+  const int64_t lo = SIGNED ? -(int64_t(1) << 31) : 0;
+  const int64_t hi = SIGNED ? (int64_t(1) << 31) - 1 : (int64_t(1) << 32) - 1;
+  if (thr > hi) return {0u, 1};
+  if (thr <= lo) return {0u, 2};
+  return {(uint32_t)thr, 0};
+}
+
+template <bool SIGNED>
+__device__ __forceinline__ bool keep_key(uint32_t k, KeepRule r) {
+  const bool lt = SIGNED ? (int32_t)k < (int32_t)r.t : k < r.t;
+  return r.mode == 0 ? lt : r.mode == 1;
+}
+
+// The count and compact passes over one tile; FULL tiles skip bounds checks.
+// Pass j covers keys [16Bj, 16B(j+1)) of the tile; warp w owns the run
+// [16Bj + 512w, + 512) of it, lane l holding keys 128q + 4l .. + 3 of the run
+// for chunks q = 0..3 (128-bit shared loads, no bank conflicts).  Order of a
+// tile: pass, warp, chunk, lane, key -- which is input order.
+template <bool FULL>
+__device__ __forceinline__ int run_index(int j, int B, int warp, int q, int lane) {
+  return 16 * B * j + 512 * warp + 128 * q + 4 * lane;
+}
+
+// Count: each lane counts its kept keys, redux.sync gives the warp's count.
+template <bool SIGNED, bool FULL>
+__device__ __forceinline__ void count_pass(const uint32_t* buf, int j, int B, int nw, int warp, int lane,
+                                           int valid, KeepRule r, uint32_t* wcnt) {
+  uint32_t c = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i0 = run_index<FULL>(j, B, warp, q, lane);
+    const uint4 v = *reinterpret_cast<const uint4*>(buf + i0);
+    c += (FULL || i0 + 0 < valid) && keep_key<SIGNED>(v.x, r);
+    c += (FULL || i0 + 1 < valid) && keep_key<SIGNED>(v.y, r);
+    c += (FULL || i0 + 2 < valid) && keep_key<SIGNED>(v.z, r);
+    c += (FULL || i0 + 3 < valid) && keep_key<SIGNED>(v.w, r);
+  }
+  c = __reduce_add_sync(kFull, c);
+  if (lane == 0) wcnt[j * nw + warp] = c;
+}
+
+// Compact: rank = warp offset + kept keys of earlier chunks of the run +
+// popc(ballot & lanemask_lt) over the chunk's four key slots + kept keys
+// before it in the lane; every kept key moves to buf[rank].
+template <bool SIGNED, bool FULL>
+__device__ __forceinline__ void compact_pass(uint32_t* buf, int j, int B, int nw, int warp, int lane, int valid,
+                                             KeepRule r, const uint32_t* wcnt, unsigned lt) {
+  uint32_t key[4][4], pos[4][4];
+  bool kp[4][4];
+  uint32_t base = wcnt[j * nw + warp];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i0 = run_index<FULL>(j, B, warp, q, lane);
+    const uint4 v = *reinterpret_cast<const uint4*>(buf + i0);
+    key[q][0] = v.x; key[q][1] = v.y; key[q][2] = v.z; key[q][3] = v.w;
+    uint32_t o = base, chunk = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      kp[q][k] = (FULL || i0 + k < valid) && keep_key<SIGNED>(key[q][k], r);
+      const unsigned b = __ballot_sync(kFull, kp[q][k]);
+      o += __popc(b & lt);
+      chunk += __popc(b);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {  // o = rank of this lane's first kept key in chunk q
+      pos[q][k] = o;
+      o += kp[q][k];
+    }
+    base += chunk;
+  }
+  __syncthreads();  // every read of pass j before any write of pass j
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (kp[q][k]) buf[pos[q][k]] = key[q][k];
+}
 
 template <bool SIGNED>
 __global__ void __launch_bounds__(1024) k_ballot_compact(const uint32_t* __restrict__ keys, int64_t n,
@@ -13,13 +124,109 @@ __global__ void __launch_bounds__(1024) k_ballot_compact(const uint32_t* __restr
                                                          int64_t* __restrict__ d_count, unsigned* ticket,
                                                          uint64_t* desc, int64_t ntiles, uint32_t limit,
                                                          unsigned* status, int vec) {
-  extern __shared__ uint32_t smem[];
-  __shared__ int64_t s_tile;
-  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);  // tiles in the order CTAs start
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int B = blockDim.x, nw = B >> 5;
+  const int64_t TILE = kBigTile;
+  const int passes = (int)(TILE / (16 * B));
+  const int m = passes * nw;                              // warp-run counts per tile: TILE / 512
+  uint32_t* buf = smem;                                   // TILE keys, compacted in place
+  uint32_t* wcnt = smem + TILE;                           // m counts, then offsets
+  uint64_t* bar = reinterpret_cast<uint64_t*>(wcnt + m);
+  __shared__ int64_t s_tile, s_prefix;
+  __shared__ uint32_t s_total;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    s_tile = atomicAdd(ticket, 1u);
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
   __syncthreads();
   const int64_t tile = s_tile;
   if (tile >= ntiles) return;
-  compact_tile<SIGNED>(keys, n, thr, out, d_count, desc, tile, ntiles, limit, status, vec, smem);
+  const int64_t base = tile * TILE;
+  const int64_t valid = min(TILE, n - base);
+  // ---- the tile into shared memory
+  const bool bulk = vec && valid == TILE;  // 16-byte aligned start, whole tile, size a multiple of 16
+  if (bulk) {
+    if (tid == 0) {
+      mbar_arrive_expect_tx(bar, (uint32_t)(TILE * 4));
+      tma_load_1d(buf, keys + base, (uint32_t)(TILE * 4), bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, 0u, limit);
+    if (__syncthreads_or(!ok)) {  // the copy did not land in time: record it, wait once more, stop
+      if (tid == 0) {
+        atomicOr(status, (unsigned)kDevTimeout);
+        mbar_wait_bounded(bar, 0u, limit);
+        st_relaxed_u64(desc + tile, kFlagP);  // successors end with a zero prefix
+      }
+      return;
+    }
+  } else {
+    for (int64_t i = tid; i < valid; i += B) buf[i] = keys[base + i];
+    __syncthreads();
+  }
+  // ---- count: pass j, chunk q holds keys j*16B + q*4B + 4t .. + 3
+  const KeepRule rule = keep_rule<SIGNED>(thr);
+  const int vlen = (int)valid;
+#pragma unroll 1
+  for (int j = 0; j < passes; ++j) {
+    if (valid == TILE) count_pass<SIGNED, true>(buf, j, B, nw, warp, lane, vlen, rule, wcnt);
+    else count_pass<SIGNED, false>(buf, j, B, nw, warp, lane, vlen, rule, wcnt);
+  }
+  __syncthreads();
+  // ---- scan of the m = 32 counts (one per lane) and the tile's count
+  if (warp == 0) {
+    const int per = (m + 31) / 32;
+    uint32_t sum = 0;
+    for (int k = 0; k < per; ++k) {
+      const int idx = lane * per + k;
+      if (idx < m) sum += wcnt[idx];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t u = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += u;
+    }
+    uint32_t ex = incl - sum;
+    for (int k = 0; k < per; ++k) {
+      const int idx = lane * per + k;
+      if (idx < m) {
+        const uint32_t c = wcnt[idx];
+        wcnt[idx] = ex;
+        ex += c;
+      }
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (lane == 0) {
+      st_relaxed_u64(desc + tile, (tile == 0 ? kFlagP : kFlagA) | total);
+      s_total = total;
+    }
+  }
+  __syncthreads();
+  // ---- compact in place, pass by pass
+  const unsigned lt = lanemask_lt();
+#pragma unroll 1
+  for (int j = 0; j < passes; ++j) {
+    if (valid == TILE) compact_pass<SIGNED, true>(buf, j, B, nw, warp, lane, vlen, rule, wcnt, lt);
+    else compact_pass<SIGNED, false>(buf, j, B, nw, warp, lane, vlen, rule, wcnt, lt);
+  }
+  // ---- prefix and copy-out
+  if (warp == 0) {
+    bool gave_up;
+    const int64_t prefix = look_back(desc, tile, s_total, limit, status, gave_up);
+    if (lane == 0) {
+      s_prefix = prefix;
+      s_bad = gave_up;
+    }
+  }
+  __syncthreads();
+  const int64_t prefix = s_prefix;
+  const uint32_t total = s_total;
+  if (s_bad || prefix + (int64_t)total > n) return;
+  for (int i = tid; i < (int)total; i += B) out[prefix + i] = buf[i];
+  if (tile == ntiles - 1 && tid == 0) *d_count = prefix + total;
 }
 
 }  // namespace cox
@@ -28,7 +235,7 @@ using namespace cox;
 
 extern "C" size_t cox_ballot_compact_workspace(int64_t n, int block_dim) {
   if (n < 0 || !valid_block(block_dim)) return 0;
-  const int64_t tile = (int64_t)block_dim * kCompactEpt;
+  const int64_t tile = kBigTile;
   const int64_t ntiles = (n + tile - 1) / tile;
   return kCompactWsHeader + (size_t)ntiles * sizeof(uint64_t);
 }
@@ -48,16 +255,15 @@ extern "C" cox_status cox_ballot_compact(cox_dtype dt, int width, int block_dim,
   if (!d_workspace || workspace_bytes < need) return COX_ENOMEM;
   if (!aligned16(d_workspace)) return COX_EINVAL;
   if (!(flags & COX_F_WS_READY) && cudaMemsetAsync(d_workspace, 0, need, st) != cudaSuccess) return COX_ECUDA;
-  const int64_t tile = (int64_t)block_dim * kCompactEpt;
+  const int64_t tile = kBigTile;
   const int64_t ntiles = (n + tile - 1) / tile;
-  if (ntiles > 0xFFFFFFFFll) return COX_EUNSUPPORTED;
-  const size_t smem = ((size_t)tile + 4 * (block_dim / 32)) * sizeof(uint32_t);
+  if (ntiles > 0xFFFFFFFFll) return COX_EUNSUPPORTED;  // 32-bit ticket
+  const size_t smem = ((size_t)tile + (size_t)(tile / 128)) * sizeof(uint32_t) + sizeof(uint64_t);
   unsigned* ticket = static_cast<unsigned*>(d_workspace);
   uint64_t* desc = reinterpret_cast<uint64_t*>(static_cast<char*>(d_workspace) + kCompactWsHeader);
   const int vec = aligned16(d_keys);
   auto launch = [&](auto kern) {
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return COX_ECUDA;
     kern<<<(unsigned)ntiles, block_dim, smem, st>>>(static_cast<const uint32_t*>(d_keys), n, threshold,
                                                   static_cast<uint32_t*>(d_out), d_count, ticket, desc, ntiles,
@@ -110,7 +316,7 @@ extern "C" cox_status cox_ballot_compact_static(cox_dtype dt, int width, int blo
   if (!valid_width(width) || !valid_block(block_dim) || n < 0) return COX_EINVAL;
   if (dt != COX_I32 && dt != COX_U32) return COX_EINVAL;
   if (!d_count || (n > 0 && (!d_keys || !d_out))) return COX_EINVAL;
-  // Larger inputs need more descriptors than the fixed scratch holds.
+  // Larger inputs need more tile descriptors than the fixed scratch holds.
   if (cox_ballot_compact_workspace(n, block_dim) > kStaticScratchBytes) return COX_ENOMEM;
   void* scratch = nullptr;
   const cox_status s = static_scratch(&scratch);

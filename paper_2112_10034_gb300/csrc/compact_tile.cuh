@@ -103,13 +103,16 @@ __device__ __forceinline__ int64_t look_back(uint64_t* desc, int64_t tile, uint3
 }
 
 // One compaction tile with the whole CTA.  `smem` holds B*16 + 4*(B/32)
-// words.  Ends with every thread past its last shared-memory access except
-// the final copy-out; callers that reuse `smem` must __syncthreads first.
+// words.  `sk`, if not null, holds the tile's B*16 keys already in shared
+// memory (a full tile); otherwise the keys are read from global memory.
+// Ends with every thread past its last shared-memory access except the
+// final copy-out; callers that reuse `smem` must __syncthreads first.
 template <bool SIGNED>
 __device__ __forceinline__ void compact_tile(const uint32_t* __restrict__ keys, int64_t n, int64_t thr,
                                              uint32_t* __restrict__ out, int64_t* __restrict__ d_count,
                                              uint64_t* desc, int64_t tile, int64_t ntiles, uint32_t limit,
-                                             unsigned* status, int vec, uint32_t* smem) {
+                                             unsigned* status, int vec, uint32_t* smem,
+                                             const uint32_t* sk = nullptr) {
   const int B = blockDim.x;
   const int nw = B >> 5;
   const int64_t TILE = (int64_t)B * kCompactEpt;
@@ -126,7 +129,12 @@ __device__ __forceinline__ void compact_tile(const uint32_t* __restrict__ keys, 
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int64_t e0 = base + (int64_t)j * 4 * B + 4 * tid;
-    if (vec && e0 + 4 <= n) {
+    if (sk) {
+      const uint4 q = *reinterpret_cast<const uint4*>(sk + (int64_t)j * 4 * B + 4 * tid);
+      key[j][0] = q.x; key[j][1] = q.y; key[j][2] = q.z; key[j][3] = q.w;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) keep[j][k] = true;
+    } else if (vec && e0 + 4 <= n) {
       const uint4 q = __ldcs(reinterpret_cast<const uint4*>(keys + e0));
       key[j][0] = q.x; key[j][1] = q.y; key[j][2] = q.z; key[j][3] = q.w;
 #pragma unroll

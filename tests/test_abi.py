@@ -52,8 +52,9 @@ def test_status_strings_and_version(cox):
 def test_workspace_sizes(cox):
     assert cox.cox_tile_reduce_workspace(cox.COX_SCOPE_TILE, 10**6, 256) == 0
     assert cox.cox_tile_reduce_workspace(cox.COX_SCOPE_GRID, 10**6, 256) > 0
-    tile = 256 * 16
+    tile = 16384
     assert cox.cox_ballot_compact_workspace(2**28, 256) == 256 + 8 * (2**28 // tile)
+    assert cox.cox_ballot_compact_workspace(2**28, 1024) == 256 + 8 * (2**28 // tile)
     assert cox.cox_ballot_compact_workspace(1, 256) == 256 + 8
 
 

@@ -270,7 +270,7 @@ def test_compaction_lookback_timeout_is_reported(cox):
     # descriptor is never published: tile 1's look-back must give up after the
     # spin limit, record COX_ETIMEOUT, and every CTA must still finish.
     import torch
-    n = 256 * 16 * 8
+    n = 16384 * 8
     k = dev(inputs.uniform_u31(n, seed=1))
     ws_bytes = cox.cox_ballot_compact_workspace(n, 256)
     ws = torch.zeros(ws_bytes // 4, dtype=torch.int32, device="cuda")
