@@ -44,7 +44,8 @@ WORKLOAD = ("tile inclusive scan (shfl_up, cg tiles) of 2^26 fp32 N(0,1) at widt
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture, valid
 # only while the kernel sources hash to `src_sha` (else reported as null).
-NCU_TRAFFIC = {"kernel": None, "src_sha": None, "bytes_per_launch": None}
+NCU_TRAFFIC = {"kernel": "k_tile_scan<Comp, 32, 16>", "src_sha": "06f10959b8357cd6",
+               "bytes_per_launch": 268510464 + 219061504}  # profiles/tile_scan_2p26_fp32_ncu.md
 KERNEL_SOURCES = ["paper_2112_10034_gb300/csrc/scan.cu", "paper_2112_10034_gb300/csrc/cox_common.cuh"]
 
 
@@ -347,7 +348,13 @@ def run_secondary(dev, st):
     ms = _time_launches(st, lambda: chk(cox.cox_match_histogram(0, 32, 256, z.data_ptr(), n, 256, hist.data_ptr(),
                                                                 None, 0, sh)))
     gbs = n * 4 / (ms * 1e-3) / 1e9
-    res["match_histogram_2p28_zipf"] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3)}
+    hres = {"ballot_peer_masks": {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3)}}
+    for name, fl in (("native_match_any", 8), ("direct_atomics_no_match", 16)):
+        ms = _time_launches(st, lambda: chk(cox.cox_match_histogram(0, 32, 256, z.data_ptr(), n, 256, hist.data_ptr(),
+                                                                    None, fl, sh)))
+        gbs = n * 4 / (ms * 1e-3) / 1e9
+        hres[name] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3)}
+    res["match_histogram_2p28_zipf"] = hres
     del z
 
     res["batched_10000_uneven"] = run_batched(dev, st)

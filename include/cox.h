@@ -75,7 +75,8 @@ enum {
   COX_F_COMPENSATED = 1u,  /* fp32 sums: TwoSum-compensated pairs through every stage */
   COX_F_FP64_COMBINE = 2u, /* GRID scope fp32 sum: final cross-block combine in FP64 */
   COX_F_WS_READY = 4u,     /* compaction: caller zeroed the workspace; skip the memset */
-  COX_F_NATIVE_MATCH = 8u  /* histograms: peer groups from the match.any.sync instruction */
+  COX_F_NATIVE_MATCH = 8u, /* histograms: peer groups from the match.any.sync instruction */
+  COX_F_DIRECT_ATOMICS = 16u /* histograms: no peer groups, one shared atomic per key */
 };
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -214,11 +215,15 @@ cox_status cox_ballot_compact_static(cox_dtype dt, int width, int block_dim, con
  * agree on a key iff they agree on every key bit), which is exactly the mask
  * __match_any_sync returns; COX_F_NATIVE_MATCH takes it from the
  * match.any.sync instruction instead (same result, slower on sm_103a).
+ * COX_F_DIRECT_ATOMICS skips the peer groups: every key adds one to its
+ * shared bin (same counts; on sm_103a shared atomics absorb Zipf-skewed keys
+ * at memory speed, so this is the fastest histogram, but it is not built
+ * from match_any).
  *   dt: COX_I32 or COX_U32 keys.  bins: 1..8192.
  *   d_hist: `bins` int32 counters, overwritten (zeroed by the call).
  *   d_ignored: optional int64 (may be NULL): number of keys outside [0, bins),
  *   overwritten.
- *   flags: 0 or COX_F_NATIVE_MATCH.
+ *   flags: 0, COX_F_NATIVE_MATCH or COX_F_DIRECT_ATOMICS.
  */
 cox_status cox_match_histogram(cox_dtype dt, int width, int block_dim, const void* d_keys, int64_t n,
                                int bins, int32_t* d_hist, int64_t* d_ignored, unsigned flags, void* stream);

@@ -22,7 +22,7 @@ COX_SUM, COX_MIN, COX_MAX, COX_AND, COX_OR, COX_XOR = range(6)
 (COX_SHFL_IDX, COX_SHFL_UP, COX_SHFL_DOWN, COX_SHFL_XOR,
  COX_BALLOT, COX_ANY, COX_ALL, COX_MATCH_ANY) = range(8)
 COX_SCOPE_TILE, COX_SCOPE_BLOCK, COX_SCOPE_GRID = 0, 1, 2
-COX_F_COMPENSATED, COX_F_FP64_COMBINE, COX_F_WS_READY, COX_F_NATIVE_MATCH = 1, 2, 4, 8
+COX_F_COMPENSATED, COX_F_FP64_COMBINE, COX_F_WS_READY, COX_F_NATIVE_MATCH, COX_F_DIRECT_ATOMICS = 1, 2, 4, 8, 16
 FULL_MASK = 0xFFFFFFFF
 
 _P = ctypes.c_void_p
@@ -299,14 +299,15 @@ def ballot_compact(keys, threshold: int, width: int = 32, block_dim: int = 256, 
 
 
 def match_histogram(keys, bins: int = 256, width: int = 32, block_dim: int = 256, unsigned: bool = False,
-                    native_match: bool = False):
+                    native_match: bool = False, direct: bool = False):
     """Match-any histogram (cox_match_histogram).  Returns (hist int32[bins], ignored int64[1])."""
     t = _torch()
     keys = _dev_tensor(keys)
     hist = t.empty(bins, dtype=t.int32, device=keys.device)
     ign = t.empty(1, dtype=t.int64, device=keys.device)
     _check(cox_match_histogram(COX_U32 if unsigned else COX_I32, width, block_dim, keys.data_ptr(), keys.numel(),
-                               bins, hist.data_ptr(), ign.data_ptr(), COX_F_NATIVE_MATCH if native_match else 0,
+                               bins, hist.data_ptr(), ign.data_ptr(),
+                               (COX_F_NATIVE_MATCH if native_match else 0) | (COX_F_DIRECT_ATOMICS if direct else 0),
                                _stream(keys.device)), "cox_match_histogram")
     return hist, ign
 

@@ -19,22 +19,31 @@ namespace cox {
 // lanes); the lowest lane of each group adds the group's size to its bin.
 // Valid keys outside the range are counted by lane 0 through one ballot --
 // the same total as summing their peer groups.
-template <int W, int BITS, bool NATIVE>
+// PEER selects how equal keys are grouped: kPeerBallot (ballots over the key
+// bits), kPeerNative (match.any.sync), kPeerNone (no grouping: every lane adds
+// one to its own bin -- the same counts, without the warp function).
+enum { kPeerBallot = 0, kPeerNative = 1, kPeerNone = 2 };
+
+template <int W, int BITS, int PEER>
 __device__ __forceinline__ void hist_step(uint32_t key, bool valid, uint32_t bins, uint32_t* my,
                                           uint32_t& ign) {
   const int lane = lane_id();
-  const unsigned tmask = W == 32 ? kFull : (((1u << W) - 1u) << (lane & ~(W - 1)));
   const bool in = valid && key < bins;
-  unsigned peers;
-  if constexpr (NATIVE) peers = __match_any_sync(kFull, key) & __ballot_sync(kFull, in);
-  else peers = match_any_bits<BITS>(key, in);
-  peers &= tmask;
-  if (in && (peers & lanemask_lt()) == 0u) atomicAdd(my + key, (uint32_t)__popc(peers));
+  if constexpr (PEER == kPeerNone) {
+    if (in) atomicAdd(my + key, 1u);
+  } else {
+    const unsigned tmask = W == 32 ? kFull : (((1u << W) - 1u) << (lane & ~(W - 1)));
+    unsigned peers;
+    if constexpr (PEER == kPeerNative) peers = __match_any_sync(kFull, key) & __ballot_sync(kFull, in);
+    else peers = match_any_bits<BITS>(key, in);
+    peers &= tmask;
+    if (in && (peers & lanemask_lt()) == 0u) atomicAdd(my + key, (uint32_t)__popc(peers));
+  }
   const unsigned out = __ballot_sync(kFull, valid && !in);
   if (lane == 0) ign += __popc(out);
 }
 
-template <int W, int BITS, bool NATIVE>
+template <int W, int BITS, int PEER>
 __global__ void __launch_bounds__(1024) k_match_hist(const uint32_t* __restrict__ keys, int64_t n, uint32_t bins,
                                                      int per_warp, int32_t* __restrict__ hist,
                                                      unsigned long long* ignored, int vec) {
@@ -55,14 +64,14 @@ __global__ void __launch_bounds__(1024) k_match_hist(const uint32_t* __restrict_
     for (; s + gws < nsteps && (s + gws + 1) * 128 <= n; s += 2 * gws) {  // two loads in flight
       const uint4 a = __ldcs(reinterpret_cast<const uint4*>(keys + s * 128) + lane);
       const uint4 b = __ldcs(reinterpret_cast<const uint4*>(keys + (s + gws) * 128) + lane);
-      hist_step<W, BITS, NATIVE>(a.x, true, bins, my, ign);
-      hist_step<W, BITS, NATIVE>(a.y, true, bins, my, ign);
-      hist_step<W, BITS, NATIVE>(a.z, true, bins, my, ign);
-      hist_step<W, BITS, NATIVE>(a.w, true, bins, my, ign);
-      hist_step<W, BITS, NATIVE>(b.x, true, bins, my, ign);
-      hist_step<W, BITS, NATIVE>(b.y, true, bins, my, ign);
-      hist_step<W, BITS, NATIVE>(b.z, true, bins, my, ign);
-      hist_step<W, BITS, NATIVE>(b.w, true, bins, my, ign);
+      hist_step<W, BITS, PEER>(a.x, true, bins, my, ign);
+      hist_step<W, BITS, PEER>(a.y, true, bins, my, ign);
+      hist_step<W, BITS, PEER>(a.z, true, bins, my, ign);
+      hist_step<W, BITS, PEER>(a.w, true, bins, my, ign);
+      hist_step<W, BITS, PEER>(b.x, true, bins, my, ign);
+      hist_step<W, BITS, PEER>(b.y, true, bins, my, ign);
+      hist_step<W, BITS, PEER>(b.z, true, bins, my, ign);
+      hist_step<W, BITS, PEER>(b.w, true, bins, my, ign);
     }
   }
   for (; s < nsteps; s += gws) {
@@ -81,7 +90,7 @@ __global__ void __launch_bounds__(1024) k_match_hist(const uint32_t* __restrict_
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) hist_step<W, BITS, NATIVE>(k[q], v[q], bins, my, ign);
+    for (int q = 0; q < 4; ++q) hist_step<W, BITS, PEER>(k[q], v[q], bins, my, ign);
   }
   if (lane == 0 && ign) atomicAdd(&s_ign, ign);
   __syncthreads();
@@ -97,10 +106,10 @@ __global__ void __launch_bounds__(1024) k_match_hist(const uint32_t* __restrict_
   if (threadIdx.x == 0 && s_ign && ignored) atomicAdd(ignored, (unsigned long long)s_ign);
 }
 
-template <int W, int BITS, bool NATIVE>
+template <int W, int BITS, int PEER>
 static cox_status launch_hist(const void* d_keys, int64_t n, int bins, int block_dim, int per_warp, size_t smem,
                               int32_t* d_hist, int64_t* d_ignored, cudaStream_t st) {
-  auto k = k_match_hist<W, BITS, NATIVE>;
+  auto k = k_match_hist<W, BITS, PEER>;
   const int nw = block_dim / 32;
   static int gmax[33][49];  // by warps per CTA and shared KiB
   int& g = gmax[nw][(smem + 1023) / 1024];
@@ -114,16 +123,16 @@ static cox_status launch_hist(const void* d_keys, int64_t n, int bins, int block
   return launch_status();
 }
 
-template <bool NATIVE>
+template <int PEER>
 static cox_status dispatch_hist(int width, const void* d_keys, int64_t n, int bins, int block_dim, int per_warp,
                                 size_t smem, int32_t* d_hist, int64_t* d_ignored, cudaStream_t st) {
   return with_width(width, [&](auto w) {
     constexpr int W = decltype(w)::value;
-    if (NATIVE || bins <= 256) return launch_hist<W, 8, NATIVE>(d_keys, n, bins, block_dim, per_warp, smem, d_hist,
-                                                                 d_ignored, st);
-    if (bins <= 1024) return launch_hist<W, 10, NATIVE>(d_keys, n, bins, block_dim, per_warp, smem, d_hist,
-                                                         d_ignored, st);
-    return launch_hist<W, 13, NATIVE>(d_keys, n, bins, block_dim, per_warp, smem, d_hist, d_ignored, st);
+    if (PEER != kPeerBallot || bins <= 256)
+      return launch_hist<W, 8, PEER>(d_keys, n, bins, block_dim, per_warp, smem, d_hist, d_ignored, st);
+    if (bins <= 1024)
+      return launch_hist<W, 10, PEER>(d_keys, n, bins, block_dim, per_warp, smem, d_hist, d_ignored, st);
+    return launch_hist<W, 13, PEER>(d_keys, n, bins, block_dim, per_warp, smem, d_hist, d_ignored, st);
   });
 }
 
@@ -137,7 +146,8 @@ extern "C" cox_status cox_match_histogram(cox_dtype dt, int width, int block_dim
   if (!valid_width(width) || !valid_block(block_dim) || n < 0) return COX_EINVAL;
   if (dt != COX_I32 && dt != COX_U32) return COX_EINVAL;
   if (bins < 1 || bins > 8192 || !d_hist || (n > 0 && !d_keys)) return COX_EINVAL;
-  if (flags & ~(unsigned)COX_F_NATIVE_MATCH) return COX_EINVAL;
+  if (flags & ~(unsigned)(COX_F_NATIVE_MATCH | COX_F_DIRECT_ATOMICS)) return COX_EINVAL;
+  if ((flags & COX_F_NATIVE_MATCH) && (flags & COX_F_DIRECT_ATOMICS)) return COX_EINVAL;
   cudaStream_t st = as_stream(stream);
   if (cudaMemsetAsync(d_hist, 0, (size_t)bins * sizeof(int32_t), st) != cudaSuccess) return COX_ECUDA;
   if (d_ignored && cudaMemsetAsync(d_ignored, 0, sizeof(int64_t), st) != cudaSuccess) return COX_ECUDA;
@@ -146,6 +156,8 @@ extern "C" cox_status cox_match_histogram(cox_dtype dt, int width, int block_dim
   const int per_warp = (size_t)nw * bins * 4 <= 48 * 1024;
   const size_t smem = (size_t)(per_warp ? nw * bins : bins) * 4;
   if (flags & COX_F_NATIVE_MATCH)
-    return dispatch_hist<true>(width, d_keys, n, bins, block_dim, per_warp, smem, d_hist, d_ignored, st);
-  return dispatch_hist<false>(width, d_keys, n, bins, block_dim, per_warp, smem, d_hist, d_ignored, st);
+    return dispatch_hist<kPeerNative>(width, d_keys, n, bins, block_dim, per_warp, smem, d_hist, d_ignored, st);
+  if (flags & COX_F_DIRECT_ATOMICS)
+    return dispatch_hist<kPeerNone>(width, d_keys, n, bins, block_dim, per_warp, smem, d_hist, d_ignored, st);
+  return dispatch_hist<kPeerBallot>(width, d_keys, n, bins, block_dim, per_warp, smem, d_hist, d_ignored, st);
 }

@@ -300,8 +300,9 @@ def test_histogram_is_bit_exact(cox, W, bins):
         z[::13] = -1
         z[5::17] = bins + 3
         want, wign = o.match_histogram(W, B, z, bins)
-        for native in (False, True):
-            hist, ign = cox.match_histogram(dev(z), bins=bins, width=W, block_dim=B, native_match=native)
+        for native, direct in ((False, False), (True, False), (False, True)):
+            hist, ign = cox.match_histogram(dev(z), bins=bins, width=W, block_dim=B, native_match=native,
+                                            direct=direct)
             np.testing.assert_array_equal(host(hist), want)
             assert int(ign.item()) == wign
 
