@@ -151,6 +151,37 @@ cox_status cox_tile_scan(cox_op op, cox_dtype dt, int width, int block_dim, cons
                          void* d_out, int64_t n, unsigned flags, void* stream);
 
 /*
+ * cox_scan -- inclusive or exclusive scan over each block (BLOCK) or over the
+ * whole array (GRID).
+ *
+ * The step after the tile scan: the SDK's shfl_scan_test scans each block
+ * with warp shuffle scans and a scan of the warp totals, and uniform_add adds
+ * each block's prefix (Table 1).  BLOCK scope does the first part on blocks
+ * of block_dim elements; GRID scope chains tiles of 16384 elements (8192 for
+ * compensated sums) with the decoupled look-back of cox_ballot_compact: in a
+ * tile every warp scans its rows of 32 elements by shfl_up, carries row
+ * totals across its rows, the warp totals are scanned, the tile publishes
+ * its aggregate, looks back for its prefix and adds it.
+ *   d_out[i] = x[s] op ... op x[i] (inclusive) or x[s] op ... op x[i-1] with
+ *   the identity at i = s (exclusive), s = the first index of i's block
+ *   (BLOCK) or 0 (GRID).
+ *   op/dt: as cox_tile_reduce; flags: COX_F_COMPENSATED for F32 SUM.
+ *   exclusive: 0 or 1.
+ *   d_workspace: GRID only, cox_scan_workspace() bytes, 16-byte aligned,
+ *   zeroed by the call (cudaMemsetAsync).  Not shared across concurrent calls.
+ * Integer results are exact.  GRID fp32 results take each tile's prefix in
+ * the order its look-back found the predecessors' values, so their last bits
+ * may differ from run to run (within the stated tolerance); BLOCK results are
+ * reproducible.  Look-back waits are bounded as in cox_ballot_compact.
+ */
+cox_status cox_scan(cox_op op, cox_dtype dt, cox_scope scope, int block_dim, const void* d_in, void* d_out,
+                    int64_t n, unsigned flags, int exclusive, void* d_workspace, size_t workspace_bytes,
+                    void* stream);
+
+/* Workspace bytes cox_scan needs (0 for BLOCK scope). */
+size_t cox_scan_workspace(cox_scope scope, int64_t n);
+
+/*
  * cox_ballot_compact -- stable stream compaction driven by warp ballots.
  *
  * The filter of the SDK's filter_arr (Table 1) with a static, full-warp group:
@@ -240,7 +271,9 @@ typedef struct {
   int ctas_per_sm;   /* persistent CTAs per SM, 1..8 */
   int width;         /* tile width of the match_any histogram step: 2..32 */
   int fp64_segments; /* arrays split over >= this many CTAs combine in FP64 (>= 1) */
-  int native_match;  /* 1: match.any.sync instruction; 0: the same peer masks from 9 ballots */
+  int native_match;  /* peer groups of the histogram step: 0 the match_any masks from 9 ballots,
+                        1 the match.any.sync instruction, 2 none (one shared atomic per key;
+                        same counts, not built from match_any) */
 } cox_batch_tune;
 
 /* Bytes of device workspace for a batch of num_arrays arrays (any tune). */

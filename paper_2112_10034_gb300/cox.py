@@ -39,6 +39,8 @@ SIGNATURES = {
     "cox_tile_reduce": (_I, [_I, _I, _I, _I, _I, _P, _P, _I64, _U, _P, _P, _SZ, _P]),
     "cox_tile_reduce_workspace": (_SZ, [_I, _I64, _I]),
     "cox_tile_scan": (_I, [_I, _I, _I, _I, _P, _P, _I64, _U, _P]),
+    "cox_scan": (_I, [_I, _I, _I, _I, _P, _P, _I64, _U, _I, _P, _SZ, _P]),
+    "cox_scan_workspace": (_SZ, [_I, _I64]),
     "cox_ballot_compact": (_I, [_I, _I, _I, _P, _I64, _I64, _P, _P, _P, _SZ, _U, _P]),
     "cox_ballot_compact_workspace": (_SZ, [_I64, _I]),
     "cox_ballot_compact_static": (_I, [_I, _I, _I, _P, _I64, _I64, _P, _P, _P]),
@@ -115,6 +117,14 @@ def cox_tile_reduce_workspace(scope, n, block_dim) -> int:
 
 def cox_tile_scan(op, dt, width, block_dim, d_in, d_out, n, flags, stream) -> int:
     return lib().cox_tile_scan(op, dt, width, block_dim, d_in, d_out, n, flags, stream)
+
+
+def cox_scan(op, dt, scope, block_dim, d_in, d_out, n, flags, exclusive, d_ws, ws_bytes, stream) -> int:
+    return lib().cox_scan(op, dt, scope, block_dim, d_in, d_out, n, flags, exclusive, d_ws, ws_bytes, stream)
+
+
+def cox_scan_workspace(scope, n) -> int:
+    return lib().cox_scan_workspace(scope, n)
 
 
 def cox_ballot_compact(dt, width, block_dim, d_keys, n, threshold, d_out, d_count, d_ws, ws_bytes, flags,
@@ -276,6 +286,23 @@ def tile_scan(x, op: int = COX_SUM, width: int = 32, block_dim: int = 256, compe
         out = t.empty_like(x)
     _check(cox_tile_scan(op, _dtype_code(x, unsigned), width, block_dim, x.data_ptr(), out.data_ptr(), x.numel(),
                          COX_F_COMPENSATED if compensated else 0, _stream(x.device)), "cox_tile_scan")
+    return out
+
+
+def scan(x, op: int = COX_SUM, scope: int = COX_SCOPE_GRID, block_dim: int = 256, compensated: bool = False,
+         exclusive: bool = False, unsigned: bool = False, out=None, workspace=None):
+    """Block- or grid-scope inclusive/exclusive scan (cox_scan)."""
+    t = _torch()
+    x = _dev_tensor(x)
+    if out is None:
+        out = t.empty_like(x)
+    ws_bytes = cox_scan_workspace(scope, x.numel())
+    if ws_bytes and workspace is None:
+        workspace = t.empty(ws_bytes, dtype=t.uint8, device=x.device)
+    _check(cox_scan(op, _dtype_code(x, unsigned), scope, block_dim, x.data_ptr(), out.data_ptr(), x.numel(),
+                    COX_F_COMPENSATED if compensated else 0, 1 if exclusive else 0,
+                    workspace.data_ptr() if workspace is not None else None, ws_bytes, _stream(x.device)),
+           "cox_scan")
     return out
 
 

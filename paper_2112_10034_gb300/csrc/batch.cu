@@ -44,16 +44,22 @@ __device__ __forceinline__ int64_t cta_of(int64_t pos, int64_t E, int64_t G) {
 // same in-range key; the lowest peer adds the group's size to the warp's bins.
 // The peer mask comes from 9 ballots over the key bits, or (NATIVE) from the
 // match.any.sync instruction: the same mask either way.
-template <int W, bool NATIVE>
+// PEER: 0 ballots over the key bits, 1 the match.any.sync instruction, 2 no
+// peer groups (one shared atomic per key; same counts).
+template <int W, int PEER>
 __device__ __forceinline__ void batch_hist_step(uint32_t key, bool valid, uint32_t* my) {
   const int lane = lane_id();
-  const unsigned tmask = W == 32 ? kFull : (((1u << W) - 1u) << (lane & ~(W - 1)));
   const bool in = valid && key < (uint32_t)kBatchBins;
-  unsigned peers;
-  if constexpr (NATIVE) peers = __match_any_sync(kFull, key) & __ballot_sync(kFull, in);
-  else peers = match_any_bits<8>(key, in);
-  peers &= tmask;
-  if (in && (peers & lanemask_lt()) == 0u) atomicAdd(my + key, (uint32_t)__popc(peers));
+  if constexpr (PEER == 2) {
+    if (in) atomicAdd(my + key, 1u);
+  } else {
+    const unsigned tmask = W == 32 ? kFull : (((1u << W) - 1u) << (lane & ~(W - 1)));
+    unsigned peers;
+    if constexpr (PEER == 1) peers = __match_any_sync(kFull, key) & __ballot_sync(kFull, in);
+    else peers = match_any_bits<8>(key, in);
+    peers &= tmask;
+    if (in && (peers & lanemask_lt()) == 0u) atomicAdd(my + key, (uint32_t)__popc(peers));
+  }
 }
 
 __device__ __forceinline__ void fold(Pair& acc, float x) { acc = Comp::op(acc, Comp::load(x)); }
@@ -61,7 +67,7 @@ __device__ __forceinline__ void fold(Pair& acc, float x) { acc = Comp::op(acc, C
 // One segment [s0, s1) of one array, all warps of the CTA.  Warp-uniform
 // loops: every lane of a warp runs every match_any step (invalid lanes take
 // part with valid = false).
-template <int W, bool NATIVE>
+template <int W, int PEER>
 __device__ void batch_segment(const float* __restrict__ v, const int32_t* __restrict__ k, int64_t s0, int64_t s1,
                               Pair& acc, uint32_t* my) {
   const int lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -75,7 +81,7 @@ __device__ void batch_segment(const float* __restrict__ v, const int32_t* __rest
       const float x = ok ? __ldcs(v + e) : 0.0f;
       const uint32_t key = ok ? (uint32_t)__ldcs(k + e) : 0u;
       if (ok) fold(acc, x);
-      batch_hist_step<W, NATIVE>(key, ok, my);
+      batch_hist_step<W, PEER>(key, ok, my);
     }
     return;
   }
@@ -90,7 +96,7 @@ __device__ void batch_segment(const float* __restrict__ v, const int32_t* __rest
     const float x = ok ? __ldcs(v + e) : 0.0f;
     const uint32_t key = ok ? (uint32_t)__ldcs(k + e) : 0u;
     if (ok) fold(acc, x);
-    batch_hist_step<W, NATIVE>(key, ok, my);
+    batch_hist_step<W, PEER>(key, ok, my);
   }
   // body: warp steps of 128 elements (one 128-bit load of values and of keys
   // per lane), two steps in flight
@@ -121,12 +127,12 @@ __device__ void batch_segment(const float* __restrict__ v, const int32_t* __rest
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       if (ok[j]) fold(acc, x[j]);
-      batch_hist_step<W, NATIVE>(key[j], ok[j], my);
+      batch_hist_step<W, PEER>(key[j], ok[j], my);
     }
   }
 }
 
-template <int W, bool NATIVE>
+template <int W, int PEER>
 __global__ void __launch_bounds__(1024) k_batch_sum_hist(const float* const* __restrict__ vals,
                                                          const int32_t* const* __restrict__ keys,
                                                          const int64_t* __restrict__ off, int64_t A,
@@ -154,7 +160,7 @@ __global__ void __launch_bounds__(1024) k_batch_sum_hist(const float* const* __r
     const int64_t base = off[a];
     const int64_t end = min(hi, off[a + 1]);
     Pair acc = Comp::ident();
-    batch_segment<W, NATIVE>(vals[a], keys[a], pos - base, end - base, acc, my);
+    batch_segment<W, PEER>(vals[a], keys[a], pos - base, end - base, acc, my);
     const Pair s = block_reduce32<Comp>(acc, wpart);  // ends with __syncthreads
     if (threadIdx.x == 0) part[a + blockIdx.x] = make_float2(s.s, s.e);
     for (int b = threadIdx.x; b < kBatchBins; b += blockDim.x) {
@@ -207,7 +213,7 @@ __global__ void k_batch_combine(const int64_t* __restrict__ off, int64_t A, int 
 bool tune_ok(const cox_batch_tune& t) {
   return t.block_dim >= 64 && t.block_dim <= 1024 && t.block_dim % 32 == 0 && t.ctas_per_sm >= 1 &&
          t.ctas_per_sm <= 8 && valid_width(t.width) && t.fp64_segments >= 1 &&
-         (t.native_match == 0 || t.native_match == 1);
+         (t.native_match >= 0 && t.native_match <= 2);
 }
 
 struct BatchWs {
@@ -269,10 +275,12 @@ extern "C" cox_status cox_batch_sum_hist(int64_t num_arrays, const float* const*
   const size_t smem = (size_t)(t.block_dim / 32) * kBatchBins * sizeof(uint32_t);
   const cox_status s = with_width(t.width, [&](auto wc) {
     constexpr int W = decltype(wc)::value;
-    if (t.native_match)
-      k_batch_sum_hist<W, true><<<G, t.block_dim, smem, st>>>(d_vals, d_keys, w.off, num_arrays, w.part, d_hists);
+    if (t.native_match == 1)
+      k_batch_sum_hist<W, 1><<<G, t.block_dim, smem, st>>>(d_vals, d_keys, w.off, num_arrays, w.part, d_hists);
+    else if (t.native_match == 2)
+      k_batch_sum_hist<W, 2><<<G, t.block_dim, smem, st>>>(d_vals, d_keys, w.off, num_arrays, w.part, d_hists);
     else
-      k_batch_sum_hist<W, false><<<G, t.block_dim, smem, st>>>(d_vals, d_keys, w.off, num_arrays, w.part, d_hists);
+      k_batch_sum_hist<W, 0><<<G, t.block_dim, smem, st>>>(d_vals, d_keys, w.off, num_arrays, w.part, d_hists);
     return launch_status();
   });
   if (s != COX_OK) return s;

@@ -137,6 +137,7 @@ struct Plain {
   __device__ static V shfl_down(V v, int d, int w) { return __shfl_down_sync(kFull, v, d, w); }
   __device__ static V shfl_up(V v, int d, int w) { return __shfl_up_sync(kFull, v, d, w); }
   __device__ static V shfl_idx(V v, int s, int w) { return __shfl_sync(kFull, v, s, w); }
+  __device__ static V shfl_xor(V v, int m) { return __shfl_xor_sync(kFull, v, m); }
   // First step on freshly loaded values (nothing to carry): same as op/shfl_up.
   __device__ static V shfl_up_fresh(V v, int d, int w) { return shfl_up(v, d, w); }
   __device__ static V op_fresh(V a, V b) { return op(a, b); }
@@ -178,6 +179,7 @@ struct Comp {
   __device__ static V shfl_idx(V v, int s, int w) {
     return {__shfl_sync(kFull, v.s, s, w), __shfl_sync(kFull, v.e, s, w)};
   }
+  __device__ static V shfl_xor(V v, int m) { return {__shfl_xor_sync(kFull, v.s, m), __shfl_xor_sync(kFull, v.e, m)}; }
   // First step on freshly loaded pairs, whose error words are all zero:
   // only s moves, and (u, 0) (+) (s, 0) = (fl(u + s), (0 + 0) + t) = (., t)
   // exactly, so the result equals op() bit for bit.

@@ -1,0 +1,392 @@
+// cox_scan: block-scope and grid-scope inclusive / exclusive scans.
+//
+// BLOCK scope follows the SDK's shfl_scan_test (Table 1 of the paper): each
+// warp scans its 32 elements with shfl_up (Hillis-Steele), warp totals go to
+// shared memory, warp 0 scans them, and every element takes its warp's
+// prefix (the uniform_add step).
+//
+// GRID scope chains tiles with a decoupled look-back.  A CTA takes a tile
+// (16384 elements; 8192 for compensated sums, whose pairs need twice the
+// shared memory) from an atomic ticket, receives it by one TMA bulk copy,
+// and every warp scans its rows of 32 elements with shfl_up, carrying row
+// totals across its rows (eight rows at a time for instruction-level
+// parallelism).  Lane 0 of warp 0 scans the eight warp totals, the tile
+// publishes its aggregate, walks back for its prefix, and every element
+// takes prefix op warp-prefix op its value.  Each tile keeps its aggregate
+// and its inclusive prefix in separate slots, each written before its flag
+// (release store) and read after it (acquire load), so a reader never sees a
+// value from the wrong stage.
+#include "cox_common.cuh"
+
+namespace cox {
+
+constexpr size_t kScanWsHeader = 256;
+constexpr int kScanLookV = 4;
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <class R>
+__device__ __forceinline__ uint64_t pack(typename R::V v) {
+  if constexpr (R::kComp) return (uint64_t)__float_as_uint(v.s) | ((uint64_t)__float_as_uint(v.e) << 32);
+  else return (uint64_t)to_bits(v);
+}
+template <class R>
+__device__ __forceinline__ typename R::V unpack(uint64_t u) {
+  using T = typename R::T;
+  if constexpr (R::kComp) return Pair{__uint_as_float((uint32_t)u), __uint_as_float((uint32_t)(u >> 32))};
+  else return from_bits<T>((uint32_t)u);
+}
+template <class R>
+__device__ __forceinline__ typename R::V warp_fold(typename R::V v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = R::op(v, R::shfl_xor(v, off));
+  return v;
+}
+
+// Look-back for generic scan values.  flags[t]: 0 nothing, 1 aggregate in
+// agg[t], 2 inclusive prefix in inc[t].  Returns the tile's exclusive prefix.
+template <class R>
+__device__ typename R::V look_back_op(uint32_t* flags, uint64_t* agg, uint64_t* inc, int64_t tile,
+                                      typename R::V total, uint32_t limit, unsigned* status, bool& gave_up) {
+  using V = typename R::V;
+  const int lane = lane_id();
+  gave_up = false;
+  if (tile == 0) {
+    if (lane == 0) {
+      st_relaxed_u64(inc, pack<R>(total));
+      st_release_u32(flags, 2u);
+    }
+    return R::ident();
+  }
+  if (lane == 0) {
+    st_relaxed_u64(agg + tile, pack<R>(total));
+    st_release_u32(flags + tile, 1u);
+  }
+  V prefix = R::ident();
+  uint32_t polls = 0;
+  bool timed_out = false;
+  for (int64_t w0 = tile - 1;; w0 -= 32 * kScanLookV) {
+    uint32_t f[kScanLookV];
+    uint64_t val[kScanLookV];
+#pragma unroll
+    for (int v = 0; v < kScanLookV; ++v) {
+      const int64_t i = w0 - (lane * kScanLookV + v);
+      f[v] = i >= 0 ? ld_acquire_u32(flags + i) : 2u;  // before tile 0: the identity
+      val[v] = 0;
+    }
+    int lp;
+    unsigned pm;
+    for (;;) {
+      lp = kScanLookV;
+#pragma unroll
+      for (int v = kScanLookV - 1; v >= 0; --v)
+        if (f[v] == 2u) lp = v;
+      pm = __ballot_sync(kFull, lp < kScanLookV);
+      const int fl = pm ? __ffs(pm) - 1 : 32;
+      bool missing = false;
+#pragma unroll
+      for (int v = 0; v < kScanLookV; ++v)
+        if ((lane < fl || (lane == fl && v <= lp)) && f[v] == 0u) missing = true;
+      if (!__any_sync(kFull, missing)) break;
+      if (++polls > limit) {
+        timed_out = true;
+        break;
+      }
+      if (polls > 64) __nanosleep(100);
+#pragma unroll
+      for (int v = 0; v < kScanLookV; ++v) {
+        const int64_t i = w0 - (lane * kScanLookV + v);
+        if (f[v] == 0u && i >= 0) f[v] = ld_acquire_u32(flags + i);
+      }
+    }
+    if (timed_out) break;
+    const int fl = pm ? __ffs(pm) - 1 : 32;
+    V part = R::ident();
+#pragma unroll
+    for (int v = kScanLookV - 1; v >= 0; --v) {  // older tiles first
+      const int64_t i = w0 - (lane * kScanLookV + v);
+      if (lane < fl || (lane == fl && v <= lp)) {
+        const V x = i < 0 ? R::ident() : unpack<R>(ld_relaxed_u64((f[v] == 2u ? inc : agg) + i));
+        part = R::op(x, part);
+      }
+    }
+    prefix = R::op(warp_fold<R>(part), prefix);
+    if (pm) break;
+  }
+  if (__any_sync(kFull, timed_out)) {
+    gave_up = true;
+    if (lane == 0) {
+      atomicOr(status, (unsigned)kDevTimeout);
+      st_relaxed_u64(inc + tile, pack<R>(total));  // release successors
+      st_release_u32(flags + tile, 2u);
+    }
+    return R::ident();
+  }
+  if (lane == 0) {
+    st_relaxed_u64(inc + tile, pack<R>(R::op(prefix, total)));
+    st_release_u32(flags + tile, 2u);
+  }
+  return prefix;
+}
+
+template <class R>
+__host__ __device__ constexpr int grid_scan_tile() {
+  return R::kComp ? 8192 : 16384;
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_scan_grid(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                   int64_t n, unsigned* ticket, uint32_t* flags, uint64_t* agg,
+                                                   uint64_t* inc, int64_t ntiles, int excl, uint32_t limit,
+                                                   unsigned* status, int vec) {
+  using T = typename R::T;
+  using V = typename R::V;
+  constexpr int TILE = grid_scan_tile<R>();
+  constexpr int NW = 8;
+  constexpr int RPW = TILE / 32 / NW;  // rows per warp
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t* bs = smem;                                        // values (or sum words)
+  float* be = reinterpret_cast<float*>(smem + TILE);          // error words (compensated)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + TILE * (R::kComp ? 2 : 1));
+  __shared__ V s_wtot[NW], s_cp[NW];
+  __shared__ int64_t s_tile;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    s_tile = atomicAdd(ticket, 1u);
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const int64_t tile = s_tile;
+  if (tile >= ntiles) return;
+  const int64_t base = tile * TILE;
+  const int valid = (int)min((int64_t)TILE, n - base);
+  if (vec && valid == TILE) {
+    if (tid == 0) {
+      mbar_arrive_expect_tx(bar, (uint32_t)(TILE * 4));
+      tma_load_1d(bs, in + base, (uint32_t)(TILE * 4), bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, 0u, limit);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(status, (unsigned)kDevTimeout);
+        mbar_wait_bounded(bar, 0u, limit);
+        st_relaxed_u64(inc + tile, pack<R>(R::ident()));
+        st_release_u32(flags + tile, 2u);
+      }
+      return;
+    }
+  } else {
+    const uint32_t pad = to_bits(R::pad());
+    for (int i = tid; i < TILE; i += blockDim.x) bs[i] = i < valid ? in[base + i] : pad;
+    __syncthreads();
+  }
+  // rows of warp w: w*RPW .. w*RPW + RPW - 1, eight at a time
+  V carry = R::ident();
+#pragma unroll 1
+  for (int g = 0; g < RPW / 8; ++g) {
+    V v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = R::load(from_bits<T>(bs[(warp * RPW + g * 8 + i) * 32 + lane]));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const V u = R::shfl_up_fresh(v[i], 1, 32);
+      if (lane >= 1) v[i] = R::op_fresh(u, v[i]);
+    }
+#pragma unroll
+    for (int d = 2; d < 32; d <<= 1) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const V u = R::shfl_up(v[i], d, 32);
+        if (lane >= d) v[i] = R::op(u, v[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {  // carry the running total into each row
+      const V tot = R::shfl_idx(v[i], 31, 32);
+      v[i] = R::op(carry, v[i]);
+      carry = R::op(carry, tot);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int idx = (warp * RPW + g * 8 + i) * 32 + lane;
+      if constexpr (R::kComp) {
+        bs[idx] = __float_as_uint(v[i].s);
+        be[idx] = v[i].e;
+      } else {
+        bs[idx] = to_bits(v[i]);
+      }
+    }
+  }
+  if (lane == 0) s_wtot[warp] = carry;
+  __syncthreads();
+  if (warp == 0) {
+    V total = R::ident();
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < NW; ++k) {
+        s_cp[k] = total;  // warp-exclusive prefix for now
+        total = R::op(total, s_wtot[k]);
+      }
+    }
+    total = R::shfl_idx(total, 0, 32);
+    bool gave_up;
+    const V prefix = look_back_op<R>(flags, agg, inc, tile, total, limit, status, gave_up);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < NW; ++k) s_cp[k] = R::op(prefix, s_cp[k]);
+      s_bad = gave_up;
+    }
+  }
+  __syncthreads();
+  if (s_bad) return;
+  const V cp = s_cp[warp];
+  auto value = [&](int idx) -> V {
+    if constexpr (R::kComp) return Pair{__uint_as_float(bs[idx]), be[idx]};
+    else return from_bits<T>(bs[idx]);
+  };
+  const int first = warp * RPW * 32;
+#pragma unroll 4
+  for (int rr = 0; rr < RPW; ++rr) {
+    const int idx = (warp * RPW + rr) * 32 + lane;
+    const int64_t gi = base + idx;
+    T y;
+    if (!excl) y = R::out(R::op(cp, value(idx)));
+    else y = idx == first ? R::out(cp) : R::out(R::op(cp, value(idx - 1)));
+    if (gi < n) out[gi] = to_bits(y);
+  }
+}
+
+// BLOCK scope: the CTA is the logical block (persistent over blocks).
+template <class R>
+__global__ void __launch_bounds__(1024) k_scan_block(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                     int64_t n, int excl) {
+  using T = typename R::T;
+  using V = typename R::V;
+  __shared__ V s_wt[32], s_wp[32];
+  const int B = blockDim.x, nw = B >> 5, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t nblk = (n + B - 1) / B;
+  for (int64_t lb = blockIdx.x; lb < nblk; lb += gridDim.x) {
+    const int64_t i = lb * B + tid;
+    V v = R::load(i < n ? from_bits<T>(__ldcs(in + i)) : R::pad());
+    {
+      const V u = R::shfl_up_fresh(v, 1, 32);
+      if (lane >= 1) v = R::op_fresh(u, v);
+    }
+#pragma unroll
+    for (int d = 2; d < 32; d <<= 1) {
+      const V u = R::shfl_up(v, d, 32);
+      if (lane >= d) v = R::op(u, v);
+    }
+    if (lane == 31) s_wt[warp] = v;
+    __syncthreads();
+    if (warp == 0) {  // exclusive scan of the warp totals
+      V w = lane < nw ? s_wt[lane] : R::ident();
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const V u = R::shfl_up(w, d, 32);
+        if (lane >= d) w = R::op(u, w);
+      }
+      const V ex = R::shfl_up(w, 1, 32);
+      s_wp[lane] = lane == 0 ? R::ident() : ex;
+    }
+    __syncthreads();
+    const V incl = R::op(s_wp[warp], v);
+    T y;
+    if (!excl) {
+      y = R::out(incl);
+    } else {
+      const V e = R::shfl_up(incl, 1, 32);
+      y = R::out(lane == 0 ? s_wp[warp] : e);
+    }
+    if (i < n) out[i] = to_bits(y);
+    __syncthreads();
+  }
+}
+
+struct ScanWs {
+  unsigned* ticket;
+  uint32_t* flags;
+  uint64_t* agg;
+  uint64_t* inc;
+};
+
+inline size_t scan_ws_bytes(int64_t ntiles) {
+  const size_t f = ((size_t)ntiles * 4 + 255) & ~(size_t)255;
+  return kScanWsHeader + f + 2 * (size_t)ntiles * 8;
+}
+
+inline ScanWs scan_ws(void* ws, int64_t ntiles) {
+  char* p = static_cast<char*>(ws);
+  ScanWs w;
+  w.ticket = reinterpret_cast<unsigned*>(p);
+  w.flags = reinterpret_cast<uint32_t*>(p + kScanWsHeader);
+  const size_t f = ((size_t)ntiles * 4 + 255) & ~(size_t)255;
+  w.agg = reinterpret_cast<uint64_t*>(p + kScanWsHeader + f);
+  w.inc = w.agg + ntiles;
+  return w;
+}
+
+template <class R>
+static cox_status launch_scan_scope(cox_scope scope, int block, const void* d_in, void* d_out, int64_t n, int excl,
+                                    void* ws, size_t ws_bytes, cudaStream_t st) {
+  const uint32_t* in = static_cast<const uint32_t*>(d_in);
+  uint32_t* out = static_cast<uint32_t*>(d_out);
+  if (scope == COX_SCOPE_BLOCK) {
+    auto k = k_scan_block<R>;
+    static int gmax[33];
+    int& g = gmax[block / 32];
+    if (g == 0) g = persistent_grid(k, block, 0, 1 << 30);
+    const int64_t nblk = (n + block - 1) / block;
+    k<<<(int)(nblk < g ? nblk : g), block, 0, st>>>(in, out, n, excl);
+    return launch_status();
+  }
+  constexpr int TILE = grid_scan_tile<R>();
+  const int64_t ntiles = (n + TILE - 1) / TILE;
+  if (ntiles > 0xFFFFFFFFll) return COX_EUNSUPPORTED;
+  const size_t need = scan_ws_bytes(ntiles);
+  if (!ws || ws_bytes < need) return COX_ENOMEM;
+  if (!aligned16(ws)) return COX_EINVAL;
+  if (cudaMemsetAsync(ws, 0, need, st) != cudaSuccess) return COX_ECUDA;
+  const ScanWs w = scan_ws(ws, ntiles);
+  auto k = k_scan_grid<R>;
+  const size_t smem = (size_t)TILE * 4 * (R::kComp ? 2 : 1) + 16;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return COX_ECUDA;
+  k<<<(unsigned)ntiles, 256, smem, st>>>(in, out, n, w.ticket, w.flags, w.agg, w.inc, ntiles, excl, spin_limit(),
+                                         device_status_word(), aligned16(d_in));
+  return launch_status();
+}
+
+}  // namespace cox
+
+using namespace cox;
+
+extern "C" size_t cox_scan_workspace(cox_scope scope, int64_t n) {
+  if (scope != COX_SCOPE_GRID || n <= 0) return 0;
+  return scan_ws_bytes((n + 8191) / 8192);  // enough for either tile size
+}
+
+extern "C" cox_status cox_scan(cox_op op, cox_dtype dt, cox_scope scope, int block_dim, const void* d_in, void* d_out,
+                               int64_t n, unsigned flags, int exclusive, void* d_workspace, size_t workspace_bytes,
+                               void* stream) {
+  if (scope != COX_SCOPE_BLOCK && scope != COX_SCOPE_GRID) return COX_EINVAL;
+  if (!valid_block(block_dim) || n < 0 || (exclusive != 0 && exclusive != 1)) return COX_EINVAL;
+  if (flags & ~(unsigned)COX_F_COMPENSATED) return COX_EINVAL;
+  if (n > 0 && (!d_in || !d_out)) return COX_EINVAL;
+  const bool comp = flags & COX_F_COMPENSATED;
+  return with_reducer(op, dt, comp, [&](auto r) {
+    using R = decltype(r);
+    if (n == 0) return COX_OK;
+    return launch_scan_scope<R>(scope, block_dim, d_in, d_out, n, exclusive, d_workspace, workspace_bytes,
+                                as_stream(stream));
+  });
+}

@@ -410,3 +410,17 @@ def test_loguniform_lengths_range():
     lens = inputs.loguniform_lengths(10000, 32, 2**20, seed=93)
     assert lens.min() >= 32 and lens.max() <= 2**20
     assert 0.85e5 < lens.mean() < 1.15e5  # mean of the log-uniform law: (b - a) / ln(b / a) ~ 1.0e5
+
+
+@pytest.mark.parametrize("L", [100, 4096, 70_001])
+def test_long_segment_scan_reference_equals_numpy(L):
+    # segments longer than a tile: the reference of block- and grid-scope scans
+    x = inputs.bits_u32(70_001, seed=L).view(np.int32)
+    bits, _, _ = o.scan_ref(o.SUM, o.I32, L, x)
+    np.testing.assert_array_equal(bits, _np_seg_scan(o.SUM, x, L))
+    f = inputs.normal_f32(70_001, seed=L + 1)
+    _, ref, ab = o.scan_ref(o.SUM, o.F32, L, f)
+    for t0 in range(0, f.size, L):
+        seg = f[t0:t0 + L].astype(np.float64)
+        want = np.cumsum(seg)  # FP64 running sum: close to the exact prefix for these sizes
+        assert np.allclose(ref[t0:t0 + L], want, rtol=0, atol=1e-9 * np.abs(seg).sum() + 1e-12)
