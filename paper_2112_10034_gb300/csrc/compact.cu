@@ -29,95 +29,6 @@
 
 namespace cox {
 
-constexpr int64_t kBigTile = 16384;  // keys per tile (64 KB); 16 * block_dim divides it for every block_dim
-
-// key < thr as one 32-bit compare: thr is clamped into the key range first
-// (every key passes if thr is above the range, none if at or below it).
-struct KeepRule {
-  uint32_t t;  // keep iff key < t in the key's own signedness...
-  int mode;    // ...when mode == 0; mode 1 keeps all, mode 2 keeps none
-};
-
-template <bool SIGNED>
-__host__ __device__ inline KeepRule keep_rule(int64_t thr) {
-  const int64_t lo = SIGNED ? -(int64_t(1) << 31) : 0;
-  const int64_t hi = SIGNED ? (int64_t(1) << 31) - 1 : (int64_t(1) << 32) - 1;
-  if (thr > hi) return {0u, 1};
-  if (thr <= lo) return {0u, 2};
-  return {(uint32_t)thr, 0};
-}
-
-template <bool SIGNED>
-__device__ __forceinline__ bool keep_key(uint32_t k, KeepRule r) {
-  const bool lt = SIGNED ? (int32_t)k < (int32_t)r.t : k < r.t;
-  return r.mode == 0 ? lt : r.mode == 1;
-}
-
-// The count and compact passes over one tile; FULL tiles skip bounds checks.
-// Pass j covers keys [16Bj, 16B(j+1)) of the tile; warp w owns the run
-// [16Bj + 512w, + 512) of it, lane l holding keys 128q + 4l .. + 3 of the run
-// for chunks q = 0..3 (128-bit shared loads, no bank conflicts).  Order of a
-// tile: pass, warp, chunk, lane, key -- which is input order.
-template <bool FULL>
-__device__ __forceinline__ int run_index(int j, int B, int warp, int q, int lane) {
-  return 16 * B * j + 512 * warp + 128 * q + 4 * lane;
-}
-
-// Count: each lane counts its kept keys, redux.sync gives the warp's count.
-template <bool SIGNED, bool FULL>
-__device__ __forceinline__ void count_pass(const uint32_t* buf, int j, int B, int nw, int warp, int lane,
-                                           int valid, KeepRule r, uint32_t* wcnt) {
-  uint32_t c = 0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i0 = run_index<FULL>(j, B, warp, q, lane);
-    const uint4 v = *reinterpret_cast<const uint4*>(buf + i0);
-    c += (FULL || i0 + 0 < valid) && keep_key<SIGNED>(v.x, r);
-    c += (FULL || i0 + 1 < valid) && keep_key<SIGNED>(v.y, r);
-    c += (FULL || i0 + 2 < valid) && keep_key<SIGNED>(v.z, r);
-    c += (FULL || i0 + 3 < valid) && keep_key<SIGNED>(v.w, r);
-  }
-  c = __reduce_add_sync(kFull, c);
-  if (lane == 0) wcnt[j * nw + warp] = c;
-}
-
-// Compact: rank = warp offset + kept keys of earlier chunks of the run +
-// popc(ballot & lanemask_lt) over the chunk's four key slots + kept keys
-// before it in the lane; every kept key moves to buf[rank].
-template <bool SIGNED, bool FULL>
-__device__ __forceinline__ void compact_pass(uint32_t* buf, int j, int B, int nw, int warp, int lane, int valid,
-                                             KeepRule r, const uint32_t* wcnt, unsigned lt) {
-  uint32_t key[4][4], pos[4][4];
-  bool kp[4][4];
-  uint32_t base = wcnt[j * nw + warp];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i0 = run_index<FULL>(j, B, warp, q, lane);
-    const uint4 v = *reinterpret_cast<const uint4*>(buf + i0);
-    key[q][0] = v.x; key[q][1] = v.y; key[q][2] = v.z; key[q][3] = v.w;
-    uint32_t o = base, chunk = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      kp[q][k] = (FULL || i0 + k < valid) && keep_key<SIGNED>(key[q][k], r);
-      const unsigned b = __ballot_sync(kFull, kp[q][k]);
-      o += __popc(b & lt);
-      chunk += __popc(b);
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {  // o = rank of this lane's first kept key in chunk q
-      pos[q][k] = o;
-      o += kp[q][k];
-    }
-    base += chunk;
-  }
-  __syncthreads();  // every read of pass j before any write of pass j
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (kp[q][k]) buf[pos[q][k]] = key[q][k];
-}
-
 template <bool SIGNED>
 __global__ void __launch_bounds__(1024) k_ballot_compact(const uint32_t* __restrict__ keys, int64_t n,
                                                          int64_t thr, uint32_t* __restrict__ out,
@@ -132,10 +43,8 @@ __global__ void __launch_bounds__(1024) k_ballot_compact(const uint32_t* __restr
   uint32_t* buf = smem;                                   // TILE keys, compacted in place
   uint32_t* wcnt = smem + TILE;                           // m counts, then offsets
   uint64_t* bar = reinterpret_cast<uint64_t*>(wcnt + m);
-  __shared__ int64_t s_tile, s_prefix;
-  __shared__ uint32_t s_total;
-  __shared__ int s_bad;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ int64_t s_tile;
+  const int tid = threadIdx.x;
   if (tid == 0) {
     s_tile = atomicAdd(ticket, 1u);
     mbar_init(bar, 1);
@@ -166,67 +75,7 @@ __global__ void __launch_bounds__(1024) k_ballot_compact(const uint32_t* __restr
     for (int64_t i = tid; i < valid; i += B) buf[i] = keys[base + i];
     __syncthreads();
   }
-  // ---- count: pass j, chunk q holds keys j*16B + q*4B + 4t .. + 3
-  const KeepRule rule = keep_rule<SIGNED>(thr);
-  const int vlen = (int)valid;
-#pragma unroll 1
-  for (int j = 0; j < passes; ++j) {
-    if (valid == TILE) count_pass<SIGNED, true>(buf, j, B, nw, warp, lane, vlen, rule, wcnt);
-    else count_pass<SIGNED, false>(buf, j, B, nw, warp, lane, vlen, rule, wcnt);
-  }
-  __syncthreads();
-  // ---- scan of the m = 32 counts (one per lane) and the tile's count
-  if (warp == 0) {
-    const int per = (m + 31) / 32;
-    uint32_t sum = 0;
-    for (int k = 0; k < per; ++k) {
-      const int idx = lane * per + k;
-      if (idx < m) sum += wcnt[idx];
-    }
-    uint32_t incl = sum;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t u = __shfl_up_sync(kFull, incl, d);
-      if (lane >= d) incl += u;
-    }
-    uint32_t ex = incl - sum;
-    for (int k = 0; k < per; ++k) {
-      const int idx = lane * per + k;
-      if (idx < m) {
-        const uint32_t c = wcnt[idx];
-        wcnt[idx] = ex;
-        ex += c;
-      }
-    }
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    if (lane == 0) {
-      st_relaxed_u64(desc + tile, (tile == 0 ? kFlagP : kFlagA) | total);
-      s_total = total;
-    }
-  }
-  __syncthreads();
-  // ---- compact in place, pass by pass
-  const unsigned lt = lanemask_lt();
-#pragma unroll 1
-  for (int j = 0; j < passes; ++j) {
-    if (valid == TILE) compact_pass<SIGNED, true>(buf, j, B, nw, warp, lane, vlen, rule, wcnt, lt);
-    else compact_pass<SIGNED, false>(buf, j, B, nw, warp, lane, vlen, rule, wcnt, lt);
-  }
-  // ---- prefix and copy-out
-  if (warp == 0) {
-    bool gave_up;
-    const int64_t prefix = look_back(desc, tile, s_total, limit, status, gave_up);
-    if (lane == 0) {
-      s_prefix = prefix;
-      s_bad = gave_up;
-    }
-  }
-  __syncthreads();
-  const int64_t prefix = s_prefix;
-  const uint32_t total = s_total;
-  if (s_bad || prefix + (int64_t)total > n) return;
-  for (int i = tid; i < (int)total; i += B) out[prefix + i] = buf[i];
-  if (tile == ntiles - 1 && tid == 0) *d_count = prefix + total;
+  compact_big_tile<SIGNED>(buf, (int)valid, thr, out, d_count, desc, tile, ntiles, n, limit, status, wcnt);
 }
 
 }  // namespace cox

@@ -10,10 +10,12 @@
 // waits on tiles with smaller indexes, which callers hand out in order to
 // CTAs that already run, so the waits end; each wait is still bounded.
 //
-// Tile layout: a CTA of B threads owns B*16 consecutive keys, read as four
-// 128-bit loads per thread; chunk j (4B keys) has thread t holding keys
-// j*4B + 4t .. 4t+3.  The rank of key (j, t, k) in the tile is
-//   offset(j, warp) + sum_k' popc(ballot_k'(j) & lanemask_lt) + #{k' < k kept}
+// Tile layout: a tile of kBigTile = 16384 keys sits in shared memory.  Warp
+// w of pass j owns the run of 512 keys at 16Bj + 512w; its lanes read them
+// as four 128-bit chunks, lane l holding keys 128q + 4l .. 128q + 4l + 3 of
+// chunk q.  The rank of a kept key in the tile is
+//   offset(j, w) + kept keys of earlier chunks of the run
+//     + sum_k' popc(ballot_k'(q) & lanemask_lt) + kept keys before it in the lane,
 // which is its position in input order, so the result is the stable filter.
 #pragma once
 
@@ -21,7 +23,6 @@
 
 namespace cox {
 
-constexpr int kCompactEpt = 16;
 constexpr size_t kCompactWsHeader = 256;
 constexpr uint64_t kFlagA = 1ull << 62;  // descriptor holds the tile's own count
 constexpr uint64_t kFlagP = 2ull << 62;  // descriptor holds the inclusive prefix
@@ -102,79 +103,131 @@ __device__ __forceinline__ int64_t look_back(uint64_t* desc, int64_t tile, uint3
   return prefix;
 }
 
-// One compaction tile with the whole CTA.  `smem` holds B*16 + 4*(B/32)
-// words.  `sk`, if not null, holds the tile's B*16 keys already in shared
-// memory (a full tile); otherwise the keys are read from global memory.
-// Ends with every thread past its last shared-memory access except the
-// final copy-out; callers that reuse `smem` must __syncthreads first.
+// ------------------------------------------------------------ big tiles
+// Compaction of one tile of up to kBigTile keys already in shared memory
+// (`buf`, valid keys at [0, valid)), with the whole CTA of B threads
+// (16 * B divides kBigTile).  `wcnt` holds kBigTile / 512 words.  Counts
+// with redux.sync, publishes the tile's count, compacts in place (a key's
+// rank never exceeds its index), looks back for the prefix and copies the
+// kept keys to out[prefix ..]; the last tile writes *d_count.
+constexpr int64_t kBigTile = 16384;  // keys per tile (64 KB); 16 * block_dim divides it for every block_dim
+
+// key < thr as one 32-bit compare: thr is clamped into the key range first
+// (every key passes if thr is above the range, none if at or below it).
+struct KeepRule {
+  uint32_t t;  // keep iff key < t in the key's own signedness...
+  int mode;    // ...when mode == 0; mode 1 keeps all, mode 2 keeps none
+};
+
 template <bool SIGNED>
-__device__ __forceinline__ void compact_tile(const uint32_t* __restrict__ keys, int64_t n, int64_t thr,
-                                             uint32_t* __restrict__ out, int64_t* __restrict__ d_count,
-                                             uint64_t* desc, int64_t tile, int64_t ntiles, uint32_t limit,
-                                             unsigned* status, int vec, uint32_t* smem,
-                                             const uint32_t* sk = nullptr) {
-  const int B = blockDim.x;
-  const int nw = B >> 5;
-  const int64_t TILE = (int64_t)B * kCompactEpt;
-  uint32_t* stage = smem;               // TILE words: the tile's kept keys, compacted
-  uint32_t* wcnt = smem + TILE;         // 4 * nw warp counts, then their offsets
+__host__ __device__ inline KeepRule keep_rule(int64_t thr) {
+  const int64_t lo = SIGNED ? -(int64_t(1) << 31) : 0;
+  const int64_t hi = SIGNED ? (int64_t(1) << 31) - 1 : (int64_t(1) << 32) - 1;
+  if (thr > hi) return {0u, 1};
+  if (thr <= lo) return {0u, 2};
+  return {(uint32_t)thr, 0};
+}
+
+template <bool SIGNED>
+__device__ __forceinline__ bool keep_key(uint32_t k, KeepRule r) {
+  const bool lt = SIGNED ? (int32_t)k < (int32_t)r.t : k < r.t;
+  return r.mode == 0 ? lt : r.mode == 1;
+}
+
+// The count and compact passes over one tile; FULL tiles skip bounds checks.
+// Pass j covers keys [16Bj, 16B(j+1)) of the tile; warp w owns the run
+// [16Bj + 512w, + 512) of it, lane l holding keys 128q + 4l .. + 3 of the run
+// for chunks q = 0..3 (128-bit shared loads, no bank conflicts).  Order of a
+// tile: pass, warp, chunk, lane, key -- which is input order.
+template <bool FULL>
+__device__ __forceinline__ int run_index(int j, int B, int warp, int q, int lane) {
+  return 16 * B * j + 512 * warp + 128 * q + 4 * lane;
+}
+
+// Count: each lane counts its kept keys, redux.sync gives the warp's count.
+template <bool SIGNED, bool FULL>
+__device__ __forceinline__ void count_pass(const uint32_t* buf, int j, int B, int nw, int warp, int lane,
+                                           int valid, KeepRule r, uint32_t* wcnt) {
+  uint32_t c = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i0 = run_index<FULL>(j, B, warp, q, lane);
+    const uint4 v = *reinterpret_cast<const uint4*>(buf + i0);
+    c += (FULL || i0 + 0 < valid) && keep_key<SIGNED>(v.x, r);
+    c += (FULL || i0 + 1 < valid) && keep_key<SIGNED>(v.y, r);
+    c += (FULL || i0 + 2 < valid) && keep_key<SIGNED>(v.z, r);
+    c += (FULL || i0 + 3 < valid) && keep_key<SIGNED>(v.w, r);
+  }
+  c = __reduce_add_sync(kFull, c);
+  if (lane == 0) wcnt[j * nw + warp] = c;
+}
+
+// Compact: rank = warp offset + kept keys of earlier chunks of the run +
+// popc(ballot & lanemask_lt) over the chunk's four key slots + kept keys
+// before it in the lane; every kept key moves to buf[rank].
+template <bool SIGNED, bool FULL>
+__device__ __forceinline__ void compact_pass(uint32_t* buf, int j, int B, int nw, int warp, int lane, int valid,
+                                             KeepRule r, const uint32_t* wcnt, unsigned lt) {
+  uint32_t key[4][4], pos[4][4];
+  bool kp[4][4];
+  uint32_t base = wcnt[j * nw + warp];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i0 = run_index<FULL>(j, B, warp, q, lane);
+    const uint4 v = *reinterpret_cast<const uint4*>(buf + i0);
+    key[q][0] = v.x; key[q][1] = v.y; key[q][2] = v.z; key[q][3] = v.w;
+    uint32_t o = base, chunk = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      kp[q][k] = (FULL || i0 + k < valid) && keep_key<SIGNED>(key[q][k], r);
+      const unsigned b = __ballot_sync(kFull, kp[q][k]);
+      o += __popc(b & lt);
+      chunk += __popc(b);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {  // o = rank of this lane's first kept key in chunk q
+      pos[q][k] = o;
+      o += kp[q][k];
+    }
+    base += chunk;
+  }
+  __syncthreads();  // every read of pass j before any write of pass j
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (kp[q][k]) buf[pos[q][k]] = key[q][k];
+}
+
+template <bool SIGNED>
+__device__ __forceinline__ void compact_big_tile(uint32_t* buf, int valid, int64_t thr, uint32_t* __restrict__ out,
+                                                 int64_t* __restrict__ d_count, uint64_t* desc, int64_t tile,
+                                                 int64_t ntiles, int64_t n, uint32_t limit, unsigned* status,
+                                                 uint32_t* wcnt) {
+  const int B = blockDim.x, nw = B >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t TILE = kBigTile;
+  const int passes = (int)(TILE / (16 * B));
+  const int m = passes * nw;
   __shared__ int64_t s_prefix;
   __shared__ uint32_t s_total;
-  __shared__ int s_gave_up;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t base = tile * TILE;
-
-  uint32_t key[4][4];
-  bool keep[4][4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int64_t e0 = base + (int64_t)j * 4 * B + 4 * tid;
-    if (sk) {
-      const uint4 q = *reinterpret_cast<const uint4*>(sk + (int64_t)j * 4 * B + 4 * tid);
-      key[j][0] = q.x; key[j][1] = q.y; key[j][2] = q.z; key[j][3] = q.w;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) keep[j][k] = true;
-    } else if (vec && e0 + 4 <= n) {
-      const uint4 q = __ldcs(reinterpret_cast<const uint4*>(keys + e0));
-      key[j][0] = q.x; key[j][1] = q.y; key[j][2] = q.z; key[j][3] = q.w;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) keep[j][k] = true;
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        keep[j][k] = e0 + k < n;
-        key[j][k] = keep[j][k] ? keys[e0 + k] : 0u;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const bool p = SIGNED ? (int64_t)(int32_t)key[j][k] < thr : (int64_t)key[j][k] < thr;
-      keep[j][k] = keep[j][k] && p;
-    }
-  }
-  uint32_t lane_pre[4];
-  const unsigned lt = lanemask_lt();
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    uint32_t cnt = 0, pre = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const unsigned b = __ballot_sync(kFull, keep[j][k]);
-      cnt += __popc(b);
-      pre += __popc(b & lt);
-    }
-    lane_pre[j] = pre;
-    if (lane == 0) wcnt[j * nw + warp] = cnt;
+  __shared__ int s_bad;
+  // ---- count: pass j, chunk q holds keys j*16B + q*4B + 4t .. + 3
+  const KeepRule rule = keep_rule<SIGNED>(thr);
+  const int vlen = valid;
+#pragma unroll 1
+  for (int j = 0; j < passes; ++j) {
+    if (valid == TILE) count_pass<SIGNED, true>(buf, j, B, nw, warp, lane, vlen, rule, wcnt);
+    else count_pass<SIGNED, false>(buf, j, B, nw, warp, lane, vlen, rule, wcnt);
   }
   __syncthreads();
-  if (warp == 0) {  // exclusive scan of the 4*nw warp counts in (chunk, warp) order
-    const int m = 4 * nw;
-    uint32_t c[4], sum = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int idx = lane * 4 + q;
-      c[q] = idx < m ? wcnt[idx] : 0u;
-      sum += c[q];
+  // ---- scan of the m = 32 counts (one per lane) and the tile's count
+  if (warp == 0) {
+    const int per = (m + 31) / 32;
+    uint32_t sum = 0;
+    for (int k = 0; k < per; ++k) {
+      const int idx = lane * per + k;
+      if (idx < m) sum += wcnt[idx];
     }
     uint32_t incl = sum;
 #pragma unroll
@@ -183,43 +236,43 @@ __device__ __forceinline__ void compact_tile(const uint32_t* __restrict__ keys, 
       if (lane >= d) incl += u;
     }
     uint32_t ex = incl - sum;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int idx = lane * 4 + q;
-      if (idx < m) wcnt[idx] = ex;
-      ex += c[q];
+    for (int k = 0; k < per; ++k) {
+      const int idx = lane * per + k;
+      if (idx < m) {
+        const uint32_t c = wcnt[idx];
+        wcnt[idx] = ex;
+        ex += c;
+      }
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
-    if (lane == 0) {  // publish the tile's count at once (its prefix if it is tile 0)
+    if (lane == 0) {
       st_relaxed_u64(desc + tile, (tile == 0 ? kFlagP : kFlagA) | total);
       s_total = total;
     }
   }
   __syncthreads();
-  // every warp stages its kept keys, compacted, in input order; warp 0 then
-  // walks back for the tile's prefix while the others are done
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    uint32_t o = wcnt[j * nw + warp] + lane_pre[j];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (keep[j][k]) stage[o++] = key[j][k];
+  // ---- compact in place, pass by pass
+  const unsigned lt = lanemask_lt();
+#pragma unroll 1
+  for (int j = 0; j < passes; ++j) {
+    if (valid == TILE) compact_pass<SIGNED, true>(buf, j, B, nw, warp, lane, vlen, rule, wcnt, lt);
+    else compact_pass<SIGNED, false>(buf, j, B, nw, warp, lane, vlen, rule, wcnt, lt);
   }
+  // ---- prefix and copy-out
   if (warp == 0) {
     bool gave_up;
     const int64_t prefix = look_back(desc, tile, s_total, limit, status, gave_up);
     if (lane == 0) {
       s_prefix = prefix;
-      s_gave_up = gave_up;
+      s_bad = gave_up;
     }
   }
   __syncthreads();
   const int64_t prefix = s_prefix;
   const uint32_t total = s_total;
-  if (s_gave_up || prefix + (int64_t)total > n) return;
-  for (int i = tid; i < (int)total; i += B) out[prefix + i] = stage[i];
+  if (s_bad || prefix + (int64_t)total > n) return;
+  for (int i = tid; i < (int)total; i += B) out[prefix + i] = buf[i];
   if (tile == ntiles - 1 && tid == 0) *d_count = prefix + total;
 }
-
 
 }  // namespace cox

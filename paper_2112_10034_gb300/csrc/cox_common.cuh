@@ -416,6 +416,22 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
+// Bulk copy from shared memory to global memory (TMA store), tracked by the
+// issuing thread's bulk async-group.  Threads that wrote the source with
+// ordinary stores must each run fence_proxy_async_smem() and then meet at a
+// barrier before one thread issues the copy.
+__device__ __forceinline__ void tma_store_1d(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+               "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Waits until the issuing thread's bulk stores have read their shared-memory
+// source (the buffer may be reused), or have completed entirely.
+__device__ __forceinline__ void tma_store_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // True once the phase with the given parity has completed.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;

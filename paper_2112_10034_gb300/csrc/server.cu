@@ -8,17 +8,18 @@
 // on the device), and marks requests done when their batch's event fires.
 //
 // Device side.  A batch is a table of request descriptors; each request is
-// cut into tiles of kTile elements, numbered consecutively request by
-// request.  Persistent CTAs take tile numbers from an atomic counter, so a
-// request's tiles are taken in order: a compaction tile only ever waits (in
-// its look-back) on smaller tiles of its own request, already taken by CTAs
-// that run.  Per tile:
-//   REDUCE  fold 16 elements per thread (TwoSum pairs for fp32), block tree,
-//           partial to the workspace; the request's last tile folds all
-//           partials in tile order.
-//   SCAN    the tile scan (scan_chunk) on 16 warp chunks of 256 elements.
-//   COMPACT the compaction tile (compact_tile), look-back over the
-//           request's own descriptors.
+// cut into tiles of kTile = 16384 elements (64 KB), numbered consecutively
+// request by request.  Persistent CTAs take tile numbers from an atomic
+// counter, so a request's tiles are taken in order: a compaction tile only
+// ever waits (in its look-back) on smaller tiles of its own request, already
+// taken by CTAs that run.  A tile arrives in shared memory by one TMA bulk
+// copy (plain loads for a ragged or unaligned tile), then:
+//   REDUCE  every thread folds its 64 elements (TwoSum pairs for fp32), a
+//           block tree gives the tile's partial; the request's last tile
+//           folds all partials in tile order;
+//   SCAN    every warp scans its 64 rows of 32 in place (shfl_up at the
+//           request's tile width) and the tile leaves by one TMA bulk store;
+//   COMPACT the big-tile compaction shared with cox_ballot_compact.
 // A request's arithmetic depends only on the request, never on its batch.
 #include <algorithm>
 #include <atomic>
@@ -37,9 +38,9 @@
 namespace cox {
 
 constexpr int kServeBlock = 256;
-constexpr int64_t kTile = kServeBlock * 16;  // 4096 elements, the compaction tile at 256 threads
-constexpr int kSlots = 3;                    // batches in flight
-constexpr int kMaxBatch = 2048;              // requests per launch
+constexpr int64_t kTile = kBigTile;  // 16384 elements per tile
+constexpr int kSlots = 3;            // batches in flight
+constexpr int kMaxBatch = 2048;      // requests per launch
 constexpr size_t kAlign = 256;
 
 struct ReqDesc {
@@ -62,33 +63,27 @@ static_assert(sizeof(BatchHdr) == 64, "batch header layout");
 
 __host__ __device__ inline int64_t serve_items(int64_t n) { return (n + kTile - 1) / kTile; }
 
-// Dynamic shared memory of k_serve: the compaction tile (kTile + 4 words per
-// warp, reused by scan staging) plus the per-request first-tile table.
-inline size_t serve_smem(size_t nreq) { return (size_t)(kTile + 4 * (kServeBlock / 32) + nreq) * 4; }
+// Dynamic shared memory of k_serve: the tile, the compaction's warp counts,
+// the mbarrier, and the per-request first-tile table.
+constexpr int kServeCounts = (int)(kTile / 512);
+inline size_t serve_smem(size_t nreq) { return (size_t)(kTile + kServeCounts + 4) * 4 + nreq * 4; }
 
 // ---------------------------------------------------------------- reduce
+// Thread t folds elements 1024 j + 4 t + k (j = 0..15, k = 0..3) of the tile,
+// in that order; elements past the request's end were loaded as 0.
 template <class R>
-__device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, typename R::V* wpart) {
+__device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, const uint32_t* buf, typename R::V* wpart) {
   using T = typename R::T;
   using V = typename R::V;
   const int tid = threadIdx.x;
-  const int64_t base = c * kTile;
-  const bool vec = (reinterpret_cast<uintptr_t>(d.in) & 15u) == 0;
   V acc = R::ident();
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int64_t e0 = base + (int64_t)j * 4 * kServeBlock + 4 * tid;
-    if (vec && e0 + 4 <= d.n) {
-      const uint4 q = __ldcs(reinterpret_cast<const uint4*>(d.in + e0));
-      acc = R::op(acc, R::load(from_bits<T>(q.x)));
-      acc = R::op(acc, R::load(from_bits<T>(q.y)));
-      acc = R::op(acc, R::load(from_bits<T>(q.z)));
-      acc = R::op(acc, R::load(from_bits<T>(q.w)));
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (e0 + k < d.n) acc = R::op(acc, R::load(from_bits<T>(d.in[e0 + k])));
-    }
+#pragma unroll 4
+  for (int j = 0; j < (int)(kTile / (4 * kServeBlock)); ++j) {
+    const uint4 q = *reinterpret_cast<const uint4*>(buf + j * 4 * kServeBlock + 4 * tid);
+    acc = R::op(acc, R::load(from_bits<T>(q.x)));
+    acc = R::op(acc, R::load(from_bits<T>(q.y)));
+    acc = R::op(acc, R::load(from_bits<T>(q.z)));
+    acc = R::op(acc, R::load(from_bits<T>(q.w)));
   }
   const V bsum = block_reduce32<R>(acc, wpart);
   unsigned* ctr = reinterpret_cast<unsigned*>(d.ws);
@@ -121,48 +116,80 @@ __device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, typename R::V* wp
 }
 
 // ------------------------------------------------------------------ scan
+// Warp w scans rows 64 w .. 64 w + 63 of the tile (row r = elements 32 r ..
+// 32 r + 31), eight at a time, by Hillis-Steele at width W, in place.
 template <class R, int W>
-__device__ void serve_scan_tile_w(const ReqDesc& d, int64_t c, uint32_t* smem) {
-  const int warp = threadIdx.x >> 5;
-  uint32_t* sm = smem + warp * 256;
-  const bool vec = ((reinterpret_cast<uintptr_t>(d.in) | reinterpret_cast<uintptr_t>(d.out)) & 15u) == 0;
+__device__ void serve_scan_rows(uint32_t* buf) {
+  using T = typename R::T;
+  using V = typename R::V;
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  const int rank = lane & (W - 1);
+  constexpr int RPW = (int)(kTile / 32 / (kServeBlock / 32));
+#pragma unroll 1
+  for (int g = 0; g < RPW / 8; ++g) {
+    V v[8];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int64_t chunk = c * (kTile / 256) + warp * 2 + h;
-    if (chunk * 256 < d.n) scan_chunk<R, W, 8>(d.in, d.out, d.n, chunk, sm, vec);
+    for (int i = 0; i < 8; ++i) v[i] = R::load(from_bits<T>(buf[(warp * RPW + g * 8 + i) * 32 + lane]));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const V u = R::shfl_up_fresh(v[i], 1, W);
+      if (rank >= 1) v[i] = R::op_fresh(u, v[i]);
+    }
+#pragma unroll
+    for (int dd = 2; dd < W; dd <<= 1) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const V u = R::shfl_up(v[i], dd, W);
+        if (rank >= dd) v[i] = R::op(u, v[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) buf[(warp * RPW + g * 8 + i) * 32 + lane] = to_bits(R::out(v[i]));
   }
 }
 
 template <class R>
-__device__ void serve_scan_tile(const ReqDesc& d, int64_t c, uint32_t* smem) {
+__device__ void serve_scan_tile(const ReqDesc& d, uint32_t* buf) {
   switch (d.width) {
-    case 2: serve_scan_tile_w<R, 2>(d, c, smem); break;
-    case 4: serve_scan_tile_w<R, 4>(d, c, smem); break;
-    case 8: serve_scan_tile_w<R, 8>(d, c, smem); break;
-    case 16: serve_scan_tile_w<R, 16>(d, c, smem); break;
-    default: serve_scan_tile_w<R, 32>(d, c, smem); break;
+    case 2: serve_scan_rows<R, 2>(buf); break;
+    case 4: serve_scan_rows<R, 4>(buf); break;
+    case 8: serve_scan_rows<R, 8>(buf); break;
+    case 16: serve_scan_rows<R, 16>(buf); break;
+    default: serve_scan_rows<R, 32>(buf); break;
   }
 }
 
-__global__ void __launch_bounds__(kServeBlock, 4) k_serve(uint8_t* table, uint32_t limit, unsigned* status) {
-  extern __shared__ uint32_t smem[];
+__global__ void __launch_bounds__(kServeBlock, 3) k_serve(uint8_t* table, uint32_t limit, unsigned* status) {
+  extern __shared__ __align__(16) uint32_t smem[];
   __shared__ Pair wpart_c[32];
   __shared__ uint32_t wpart_u[32];
   __shared__ float wpart_f[32];
   __shared__ int64_t s_item;
   __shared__ int s_req;
+  uint32_t* buf = smem;                                           // the tile
+  uint32_t* wcnt = smem + kTile;                                  // compaction warp counts
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kTile + kServeCounts);
+  uint32_t* first = smem + kTile + kServeCounts + 4;              // first tile of every request
   BatchHdr* hdr = reinterpret_cast<BatchHdr*>(table);
   const ReqDesc* reqs = reinterpret_cast<const ReqDesc*>(table + sizeof(BatchHdr));
   const int64_t nitems = hdr->nitems;
   const int nreq = hdr->nreq;
-  // First tile of every request, staged once per CTA so that finding a tile's
-  // request is a binary search in shared memory (tile numbers fit 32 bits:
-  // a batch holds at most kMaxBatch requests of < 2^31 tiles in total).
-  uint32_t* first = smem + kTile + 4 * (kServeBlock / 32);
-  for (int r = threadIdx.x; r < nreq; r += blockDim.x) first[r] = (uint32_t)reqs[r].item0;
+  const int tid = threadIdx.x;
+  // Tile numbers fit 32 bits: a batch holds at most kMaxBatch requests of
+  // fewer than 2^31 elements each.
+  for (int r = tid; r < nreq; r += blockDim.x) first[r] = (uint32_t)reqs[r].item0;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  uint32_t loads = 0;  // bulk copies completed on `bar`
   for (;;) {
-    __syncthreads();  // the previous tile is done with shared memory
-    if (threadIdx.x == 0) {
+    // Every thread's accesses to the tile, ordered before the async proxy's
+    // next write to it; the previous tile's bulk store has read the tile.
+    fence_proxy_async_smem();
+    if (tid == 0) tma_store_wait_read();
+    __syncthreads();
+    if (tid == 0) {
       const int64_t item = (int64_t)atomicAdd(&hdr->next, 1ull);
       s_item = item;
       if (item < nitems) {
@@ -177,33 +204,64 @@ __global__ void __launch_bounds__(kServeBlock, 4) k_serve(uint8_t* table, uint32
     }
     __syncthreads();
     const int64_t item = s_item;
-    if (item >= nitems) return;
+    if (item >= nitems) break;
     const ReqDesc d = reqs[s_req];
     const int64_t c = item - d.item0;
+    const int64_t base = c * kTile;
+    const int valid = (int)min(kTile, d.n - base);
+    // ---- the tile into shared memory (0 past the request's end: the sums' identity)
+    if (valid == kTile && (reinterpret_cast<uintptr_t>(d.in) & 15u) == 0) {
+      if (tid == 0) {
+        mbar_arrive_expect_tx(bar, (uint32_t)(kTile * 4));
+        tma_load_1d(buf, d.in + base, (uint32_t)(kTile * 4), bar);
+      }
+      const bool ok = mbar_wait_bounded(bar, loads & 1u, limit);
+      ++loads;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicOr(status, (unsigned)kDevTimeout);
+          mbar_wait_bounded(bar, (loads - 1) & 1u, limit);  // the copy in flight, before the CTA ends
+        }
+        break;
+      }
+    } else {
+      for (int i = tid; i < (int)kTile; i += blockDim.x) buf[i] = i < valid ? d.in[base + i] : 0u;
+      __syncthreads();
+    }
     if (d.kind == COX_REQ_REDUCE) {
       if (d.dt == COX_F32) {
-        if (d.flags & COX_F_COMPENSATED) serve_reduce_tile<Comp>(d, c, wpart_c);
-        else serve_reduce_tile<Plain<AddF>>(d, c, wpart_f);
+        if (d.flags & COX_F_COMPENSATED) serve_reduce_tile<Comp>(d, c, buf, wpart_c);
+        else serve_reduce_tile<Plain<AddF>>(d, c, buf, wpart_f);
       } else {
-        serve_reduce_tile<Plain<AddU>>(d, c, wpart_u);
+        serve_reduce_tile<Plain<AddU>>(d, c, buf, wpart_u);
       }
     } else if (d.kind == COX_REQ_SCAN) {
       if (d.dt == COX_F32) {
-        if (d.flags & COX_F_COMPENSATED) serve_scan_tile<Comp>(d, c, smem);
-        else serve_scan_tile<Plain<AddF>>(d, c, smem);
+        if (d.flags & COX_F_COMPENSATED) serve_scan_tile<Comp>(d, buf);
+        else serve_scan_tile<Plain<AddF>>(d, buf);
       } else {
-        serve_scan_tile<Plain<AddU>>(d, c, smem);
+        serve_scan_tile<Plain<AddU>>(d, buf);
+      }
+      uint32_t* dst = d.out + base;
+      if (valid == kTile && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+        fence_proxy_async_smem();  // this thread's stores to the tile, before the bulk copy reads it
+        __syncthreads();
+        if (tid == 0) tma_store_1d(dst, buf, (uint32_t)(kTile * 4));
+      } else {
+        __syncthreads();
+        for (int i = tid; i < valid; i += blockDim.x) dst[i] = buf[i];
       }
     } else {
       int64_t* count = reinterpret_cast<int64_t*>(d.ws);
       uint64_t* desc = reinterpret_cast<uint64_t*>(d.ws + kAlign);
-      const int vec = (reinterpret_cast<uintptr_t>(d.in) & 15u) == 0;
       if (d.dt == COX_I32)
-        compact_tile<true>(d.in, d.n, d.threshold, d.out, count, desc, c, d.nitems, limit, status, vec, smem);
+        compact_big_tile<true>(buf, valid, d.threshold, d.out, count, desc, c, d.nitems, d.n, limit, status, wcnt);
       else
-        compact_tile<false>(d.in, d.n, d.threshold, d.out, count, desc, c, d.nitems, limit, status, vec, smem);
+        compact_big_tile<false>(buf, valid, d.threshold, d.out, count, desc, c, d.nitems, d.n, limit, status,
+                                wcnt);
     }
   }
+  if (tid == 0) tma_store_wait_all();  // no bulk store outlives the CTA
 }
 
 // Zeroes what each request's tiles expect at zero: the reduce counter, the
