@@ -25,6 +25,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <map>
 #include <mutex>
@@ -58,8 +59,10 @@ struct BatchHdr {
   int64_t nitems;
   int nreq;
   int pad[11];
-};  // 64 bytes, followed by nreq ReqDesc
+};  // 64 bytes, followed by nreq ReqDesc, then nreq tile counters (zeroed by the host)
 static_assert(sizeof(BatchHdr) == 64, "batch header layout");
+
+inline size_t table_bytes(size_t nreq) { return sizeof(BatchHdr) + nreq * (sizeof(ReqDesc) + sizeof(unsigned)); }
 
 __host__ __device__ inline int64_t serve_items(int64_t n) { return (n + kTile - 1) / kTile; }
 
@@ -72,7 +75,8 @@ inline size_t serve_smem(size_t nreq) { return (size_t)(kTile + kServeCounts + 4
 // Thread t folds elements 1024 j + 4 t + k (j = 0..15, k = 0..3) of the tile,
 // in that order; elements past the request's end were loaded as 0.
 template <class R>
-__device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, const uint32_t* buf, typename R::V* wpart) {
+__device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, const uint32_t* buf, typename R::V* wpart,
+                                  unsigned* ctr) {
   using T = typename R::T;
   using V = typename R::V;
   const int tid = threadIdx.x;
@@ -86,8 +90,7 @@ __device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, const uint32_t* b
     acc = R::op(acc, R::load(from_bits<T>(q.w)));
   }
   const V bsum = block_reduce32<R>(acc, wpart);
-  unsigned* ctr = reinterpret_cast<unsigned*>(d.ws);
-  V* part = reinterpret_cast<V*>(d.ws + kAlign);
+  V* part = reinterpret_cast<V*>(d.ws);
   __shared__ int s_last;
   if (tid == 0) {
     part[c] = bsum;
@@ -174,6 +177,7 @@ __global__ void __launch_bounds__(kServeBlock, 3) k_serve(uint8_t* table, uint32
   const ReqDesc* reqs = reinterpret_cast<const ReqDesc*>(table + sizeof(BatchHdr));
   const int64_t nitems = hdr->nitems;
   const int nreq = hdr->nreq;
+  unsigned* ctrs = reinterpret_cast<unsigned*>(table + sizeof(BatchHdr) + (size_t)nreq * sizeof(ReqDesc));
   const int tid = threadIdx.x;
   // Tile numbers fit 32 bits: a batch holds at most kMaxBatch requests of
   // fewer than 2^31 elements each.
@@ -230,10 +234,10 @@ __global__ void __launch_bounds__(kServeBlock, 3) k_serve(uint8_t* table, uint32
     }
     if (d.kind == COX_REQ_REDUCE) {
       if (d.dt == COX_F32) {
-        if (d.flags & COX_F_COMPENSATED) serve_reduce_tile<Comp>(d, c, buf, wpart_c);
-        else serve_reduce_tile<Plain<AddF>>(d, c, buf, wpart_f);
+        if (d.flags & COX_F_COMPENSATED) serve_reduce_tile<Comp>(d, c, buf, wpart_c, ctrs + s_req);
+        else serve_reduce_tile<Plain<AddF>>(d, c, buf, wpart_f, ctrs + s_req);
       } else {
-        serve_reduce_tile<Plain<AddU>>(d, c, buf, wpart_u);
+        serve_reduce_tile<Plain<AddU>>(d, c, buf, wpart_u, ctrs + s_req);
       }
     } else if (d.kind == COX_REQ_SCAN) {
       if (d.dt == COX_F32) {
@@ -264,15 +268,15 @@ __global__ void __launch_bounds__(kServeBlock, 3) k_serve(uint8_t* table, uint32
   if (tid == 0) tma_store_wait_all();  // no bulk store outlives the CTA
 }
 
-// Zeroes what each request's tiles expect at zero: the reduce counter, the
-// compaction count and look-back descriptors.
+// Zeroes the look-back descriptors of every compaction request of a batch
+// (launched only for batches that hold one).
 __global__ void k_serve_prep(const uint8_t* __restrict__ table) {
   const BatchHdr* hdr = reinterpret_cast<const BatchHdr*>(table);
   const ReqDesc* reqs = reinterpret_cast<const ReqDesc*>(table + sizeof(BatchHdr));
   if ((int)blockIdx.x >= hdr->nreq) return;
   const ReqDesc d = reqs[blockIdx.x];
-  if (d.kind == COX_REQ_SCAN) return;
-  const size_t words = d.kind == COX_REQ_COMPACT ? (kAlign + (size_t)d.nitems * 8) / 4 : kAlign / 4;
+  if (d.kind != COX_REQ_COMPACT) return;
+  const size_t words = (kAlign + (size_t)d.nitems * 8) / 4;
   uint32_t* w = reinterpret_cast<uint32_t*>(d.ws);
   for (size_t i = threadIdx.x; i < words; i += blockDim.x) w[i] = 0u;
 }
@@ -289,7 +293,7 @@ size_t round_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 void request_bytes(const cox_request& r, size_t* out_b, size_t* ws_b) {
   const int64_t items = serve_items(r.n);
   switch (r.kind) {
-    case COX_REQ_REDUCE: *out_b = kAlign; *ws_b = kAlign + round_up((size_t)items * 8); break;
+    case COX_REQ_REDUCE: *out_b = kAlign; *ws_b = round_up((size_t)items * 8); break;
     case COX_REQ_SCAN: *out_b = round_up((size_t)r.n * 4); *ws_b = 0; break;
     default: *out_b = round_up((size_t)r.n * 4); *ws_b = kAlign + round_up((size_t)items * 8); break;
   }
@@ -357,8 +361,13 @@ struct SReq {
   cox_request r;
   ReqState state = kQueued;
   size_t off = 0, bytes = 0, out_b = 0, held = 0;
-  double t_done = 0.0;
+  double t_ready = 0.0, t_done = 0.0;
 };
+
+// While a batch runs, admitted requests wait for the next launch until they
+// fill the persistent grid with tiles or the oldest has waited this long:
+// fewer, larger batches under load, no added wait when the device is idle.
+constexpr double kBatchDelay = 20e-6;
 
 struct Slot {
   cudaStream_t st = nullptr;
@@ -395,10 +404,14 @@ struct cox_server {
   uint64_t next_ticket = 1;
   cox_server_stats stats{};
 
-  void launch_batch(Slot& sl, const std::vector<uint64_t>& ts) {
+  // Writes the batch table of `ts` into the slot's pinned host buffer and
+  // marks the requests running (caller holds `mu`).  Returns the table size
+  // and sets *items and *has_compact.
+  size_t fill_batch(Slot& sl, const std::vector<uint64_t>& ts, int64_t* items_out, bool* has_compact) {
     BatchHdr* h = reinterpret_cast<BatchHdr*>(sl.host_tab);
     ReqDesc* d = reinterpret_cast<ReqDesc*>(sl.host_tab + sizeof(BatchHdr));
     int64_t items = 0;
+    bool compact = false;
     for (size_t i = 0; i < ts.size(); ++i) {
       SReq& q = reqs[ts[i]];
       ReqDesc& e = d[i];
@@ -414,43 +427,56 @@ struct cox_server {
       e.item0 = items;
       e.nitems = serve_items(q.r.n);
       items += e.nitems;
+      compact = compact || q.r.kind == COX_REQ_COMPACT;
       q.state = kRunning;
     }
     // (requests are < 2^31 elements each, so 2048 of them stay < 2^31 tiles)
+    std::memset(sl.host_tab + sizeof(BatchHdr) + ts.size() * sizeof(ReqDesc), 0, ts.size() * sizeof(unsigned));
     h->next = 0;
     h->nitems = items;
     h->nreq = (int)ts.size();
-    const size_t tab_bytes = sizeof(BatchHdr) + ts.size() * sizeof(ReqDesc);
-    bool ok = cudaMemcpyAsync(sl.dev_tab, sl.host_tab, tab_bytes, cudaMemcpyHostToDevice, sl.st) == cudaSuccess;
-    if (ok) {
-      k_serve_prep<<<(unsigned)ts.size(), 256, 0, sl.st>>>(sl.dev_tab);
-      const int g = (int)std::min<int64_t>(grid, items);
-      const size_t smem = serve_smem(ts.size());
-      k_serve<<<g, kServeBlock, smem, sl.st>>>(sl.dev_tab, spin_limit(), device_status_word());
-      ok = cudaGetLastError() == cudaSuccess && cudaEventRecord(sl.ev, sl.st) == cudaSuccess;
-    }
     sl.tickets = ts;
     sl.busy = true;
     stats.batches += 1;
     stats.max_batch = std::max<int64_t>(stats.max_batch, (int64_t)ts.size());
-    if (!ok) {  // the batch's requests fail; the event query below reports them
-      for (uint64_t t : ts) reqs[t].state = kFailed;
-      sl.busy = false;
-      stats.failed += (int64_t)ts.size();
-      cv.notify_all();
+    *items_out = items;
+    *has_compact = compact;
+    return table_bytes(ts.size());
+  }
+
+  // Enqueues a filled batch on the slot's stream (without `mu`: submitters
+  // are not held up by the launch calls).
+  bool issue_batch(Slot& sl, size_t tab_bytes, int64_t items, bool has_compact) {
+    bool ok = cudaMemcpyAsync(sl.dev_tab, sl.host_tab, tab_bytes, cudaMemcpyHostToDevice, sl.st) == cudaSuccess;
+    if (ok) {
+      const int nreq = reinterpret_cast<BatchHdr*>(sl.host_tab)->nreq;
+      if (has_compact) k_serve_prep<<<(unsigned)nreq, 256, 0, sl.st>>>(sl.dev_tab);
+      const int g = (int)std::min<int64_t>(grid, items);
+      k_serve<<<g, kServeBlock, serve_smem((size_t)nreq), sl.st>>>(sl.dev_tab, spin_limit(), device_status_word());
+      ok = cudaGetLastError() == cudaSuccess && cudaEventRecord(sl.ev, sl.st) == cudaSuccess;
     }
+    return ok;
   }
 
   void loop() {
     cudaSetDevice(dev);
+    int64_t ready_items = 0;  // tiles of the admitted, not yet launched requests
     while (!stop.load(std::memory_order_relaxed)) {
       bool progress = false;
+      Slot* launch = nullptr;
+      size_t tab_bytes = 0;
+      int64_t items = 0;
+      bool has_compact = false;
       {
         std::lock_guard<std::mutex> g(mu);
+        int inflight = 0;
         for (Slot& sl : slots) {  // completions
           if (!sl.busy) continue;
           const cudaError_t e = cudaEventQuery(sl.ev);
-          if (e == cudaErrorNotReady) continue;
+          if (e == cudaErrorNotReady) {
+            ++inflight;
+            continue;
+          }
           const double t = now_s();
           for (uint64_t tk : sl.tickets) {
             auto it = reqs.find(tk);
@@ -466,29 +492,49 @@ struct cox_server {
           progress = true;
           cv.notify_all();
         }
+        const double now = now_s();
         while (!queue.empty() && admitted < max_req) {  // admission, in arrival order
           SReq& q = reqs[queue.front()];
           size_t off;
           if (used + q.held > budget || !arena->alloc(q.bytes, &off)) break;
           q.off = off;
           q.state = kReady;
+          q.t_ready = now;
           used += q.held;
           peak = std::max(peak, used);
           ++admitted;
+          ready_items += serve_items(q.r.n);
           ready.push_back(queue.front());
           queue.pop_front();
           progress = true;
         }
-        if (!ready.empty()) {  // launch everything admitted on a free stream
+        const bool go = !ready.empty() && inflight < kSlots &&
+                        (inflight == 0 || ready_items >= grid || now - reqs[ready.front()].t_ready >= kBatchDelay);
+        if (go) {
           for (Slot& sl : slots) {
             if (sl.busy) continue;
             const size_t k = std::min<size_t>(ready.size(), kMaxBatch);
             std::vector<uint64_t> ts(ready.begin(), ready.begin() + k);
             ready.erase(ready.begin(), ready.begin() + k);
-            launch_batch(sl, ts);
-            progress = true;
+            tab_bytes = fill_batch(sl, ts, &items, &has_compact);
+            ready_items -= items;
+            launch = &sl;
             break;
           }
+        }
+      }
+      if (launch) {
+        progress = true;
+        if (!issue_batch(*launch, tab_bytes, items, has_compact)) {
+          // The batch's requests fail.  What did get enqueued ends before the
+          // slot's table is written again.
+          cudaStreamSynchronize(launch->st);
+          std::lock_guard<std::mutex> g(mu);
+          for (uint64_t t : launch->tickets) reqs[t].state = kFailed;
+          stats.failed += (int64_t)launch->tickets.size();
+          launch->tickets.clear();
+          launch->busy = false;
+          cv.notify_all();
         }
       }
       if (!progress) std::this_thread::yield();
@@ -512,7 +558,7 @@ extern "C" cox_status cox_server_create(size_t budget_bytes, int max_requests, c
     return COX_ENOMEM;
   }
   s->arena = new Arena(s->budget);
-  const size_t tab = sizeof(BatchHdr) + (size_t)kMaxBatch * sizeof(ReqDesc);
+  const size_t tab = table_bytes(kMaxBatch);
   for (Slot& sl : s->slots) {
     if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
@@ -697,8 +743,9 @@ extern "C" cox_status cox_server_run_trace(cox_server* s, const cox_trace_item* 
       index.erase(it);
       ++done;
     }
+    const bool idle = fin.empty();
     fin.clear();
-    if (fin.empty() && next < count) std::this_thread::yield();
+    if (idle) std::this_thread::yield();
   }
   {
     std::lock_guard<std::mutex> g(s->mu);
