@@ -1,8 +1,8 @@
 """Throughput benchmark of the warp-collective library on one GB300.
 
-A step is the tile-scan workload: cooperative-groups inclusive scans by
-shfl_up over 2^26 fp32 values ~ N(0,1) at tile widths 4, 8, 16 and 32, each
-plain and TwoSum-compensated, 256-thread blocks (8 launches per step).  The
+A step is the tile-scan workload: cooperative-groups inclusive scans (the
+shfl_up Hillis-Steele scan) over 2^26 fp32 values ~ N(0,1) at tile widths 4,
+8, 16 and 32, each plain and TwoSum-compensated (8 launches per step).  The
 metric is warp-collective GB/s: algorithmic bytes (4 read + 4 written per
 element per launch) over device time, and its fraction of the measured HBM
 copy bandwidth.  The JSON line also carries the dominant kernel's roofline,
@@ -44,8 +44,8 @@ WORKLOAD = ("tile inclusive scan (shfl_up, cg tiles) of 2^26 fp32 N(0,1) at widt
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture, valid
 # only while the kernel sources hash to `src_sha` (else reported as null).
-NCU_TRAFFIC = {"kernel": "k_tile_scan<Comp, 32, 16>", "src_sha": "06f10959b8357cd6",
-               "bytes_per_launch": 268510464 + 219061504}  # profiles/tile_scan_2p26_fp32_ncu.md
+NCU_TRAFFIC = {"kernel": "k_tile_scan_rows<Comp, 32>", "src_sha": "6c43a17ef0f4328a",
+               "bytes_per_launch": 268489728 + 217476352}  # profiles/tile_scan_2p26_fp32_ncu.md
 KERNEL_SOURCES = ["paper_2112_10034_gb300/csrc/scan.cu", "paper_2112_10034_gb300/csrc/cox_common.cuh"]
 
 
@@ -201,7 +201,9 @@ def run_cox(args):
     dom = int(np.argmax(per_variant_ms))
     achieved = BYTES_PER_LAUNCH / (per_variant_ms[dom] * 1e-3) / 1e9
     w_dom, c_dom = VARIANTS[dom]
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["src_sha"] == _src_sha() else None
+    dom_name = f"k_tile_scan_rows<{'Comp' if c_dom else 'Plain<AddF>'}, {w_dom}>"
+    traffic = (NCU_TRAFFIC["bytes_per_launch"]
+               if NCU_TRAFFIC["src_sha"] == _src_sha() and NCU_TRAFFIC["kernel"] == dom_name else None)
 
     # ---- end to end through host buffers (pinned), copies inside the region
     e2e = run_e2e(args, x_host, dev, st, min(K, 20))
@@ -223,7 +225,7 @@ def run_cox(args):
                    "launches_per_step": len(VARIANTS), "parallelism": f"replicas x{world}",
                    "l2": "no flush: each launch streams 256 MiB in + 256 MiB out, > 129 MB L2"},
         "frac_of_hbm": round(value / world / peak, 4),
-        "roofline": {"bound": "hbm", "kernel": f"k_tile_scan<{'Comp' if c_dom else 'Plain<AddF>'},W={w_dom}>",
+        "roofline": {"bound": "hbm", "kernel": dom_name,
                      "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "algorithmic_bytes_per_launch": BYTES_PER_LAUNCH},

@@ -221,6 +221,32 @@ def test_tile_scan_matches_the_emulation(cox, dt, op, W):
 
 
 @pytest.mark.parametrize("W", WIDTHS)
+@pytest.mark.parametrize("comp", [False, True])
+def test_tile_scan_row_path_sizes_and_alignment(cox, W, comp):
+    """Aligned arrays of >= 32 elements take the row-per-lane TMA kernel: whole
+    rows, partial chunks of rows, a partial last row, and three chunks per
+    persistent warp (the 2^26 test below cycles each warp's ring many times);
+    arrays offset by 4 bytes take the shuffle kernel.  Both give the
+    emulation's bits."""
+    import torch
+    sizes = (32, 33, 1024, 1024 + 31, 32 * 45 + 7, 2432 * 1024 * 3 + 32 * 5 + 9)
+    flags = cox.COX_F_COMPENSATED if comp else 0
+    for n in sizes:
+        x = inputs.normal_f32(n, seed=n + 3 * W + comp)
+        for off in (0, 1):
+            xd = torch.zeros(n + 8, dtype=torch.float32, device="cuda")
+            xd[off:off + n] = dev(x)
+            out = poisoned(n + 8, torch.int32)
+            assert cox.cox_tile_scan(o.SUM, o.F32, W, 256, xd.data_ptr() + 4 * off, out.data_ptr() + 4 * off, n,
+                                     flags, None) == 0
+            got = host(out)
+            want = o.scan_emulate(o.SUM, o.F32, W, 256, x, comp)
+            np.testing.assert_array_equal(got[off:off + n].view(np.uint32), want.view(np.uint32))
+            assert (got[:off] == POISON).all() and (got[off + n:] == POISON).all()
+    assert cox.device_status() == cox.COX_OK
+
+
+@pytest.mark.parametrize("W", WIDTHS)
 def test_compensated_scan_bits_and_error(cox, W):
     n = 256 * 8 * 10 + 3
     x = inputs.normal_f32(n, seed=77 + W)
