@@ -44,8 +44,11 @@ WORKLOAD = ("tile inclusive scan (shfl_up, cg tiles) of 2^26 fp32 N(0,1) at widt
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture, valid
 # only while the kernel sources hash to `src_sha` (else reported as null).
-NCU_TRAFFIC = {"kernel": "k_tile_scan_rows<Comp, 32>", "src_sha": "6c43a17ef0f4328a",
-               "bytes_per_launch": 268489728 + 217476352}  # profiles/tile_scan_2p26_fp32_ncu.md
+NCU_TRAFFIC = {"src_sha": "6c43a17ef0f4328a",  # profiles/tile_scan_2p26_fp32_ncu.md
+               "bytes_per_launch": {"k_tile_scan_rows<Comp, 32>": 268489728 + 217500416,
+                                    "k_tile_scan_rows<Comp, 16>": 268482560 + 216888832,
+                                    "k_tile_scan_rows<Plain<AddF>, 32>": 268497152 + 216726528,
+                                    "k_tile_scan_rows<Plain<AddF>, 16>": 268458496 + 217366784}}
 KERNEL_SOURCES = ["paper_2112_10034_gb300/csrc/scan.cu", "paper_2112_10034_gb300/csrc/cox_common.cuh"]
 
 
@@ -202,8 +205,7 @@ def run_cox(args):
     achieved = BYTES_PER_LAUNCH / (per_variant_ms[dom] * 1e-3) / 1e9
     w_dom, c_dom = VARIANTS[dom]
     dom_name = f"k_tile_scan_rows<{'Comp' if c_dom else 'Plain<AddF>'}, {w_dom}>"
-    traffic = (NCU_TRAFFIC["bytes_per_launch"]
-               if NCU_TRAFFIC["src_sha"] == _src_sha() and NCU_TRAFFIC["kernel"] == dom_name else None)
+    traffic = NCU_TRAFFIC["bytes_per_launch"].get(dom_name) if NCU_TRAFFIC["src_sha"] == _src_sha() else None
 
     # ---- end to end through host buffers (pinned), copies inside the region
     e2e = run_e2e(args, x_host, dev, st, min(K, 20))
@@ -248,39 +250,69 @@ def run_cox(args):
 
 def run_e2e(args, x_host, dev, st, K):
     """Same metric through the C ABI with host buffers: per step, the input goes
-    host->device from pinned memory and all 8 outputs come back device->host."""
+    host->device from pinned memory and all 8 outputs come back device->host.
+    Steps are pipelined the way a streaming caller would run them: the input
+    copy, the scans and the output copies sit on three streams ordered by
+    events, so step k's output copies overlap step k+1's input copy and scans
+    (the input is double-buffered; an output buffer is rewritten only after
+    its previous copy to the host has finished)."""
     import torch
     from paper_2112_10034_gb300 import cox
     pin_in = torch.from_numpy(x_host).pin_memory()
     pin_out = [torch.empty(N_ELEMS, dtype=torch.float32).pin_memory() for _ in VARIANTS]
-    x = torch.empty(N_ELEMS, dtype=torch.float32, device=dev)
+    xs = [torch.empty(N_ELEMS, dtype=torch.float32, device=dev) for _ in range(2)]
     outs = [torch.empty(N_ELEMS, dtype=torch.float32, device=dev) for _ in VARIANTS]
+    s_h2d, s_d2h = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
     sh = st.cuda_stream
+    ev = lambda: torch.cuda.Event()
+    x_free = [ev(), ev()]          # scans of the step that last used xs[b] are done
+    x_ready = [ev(), ev()]         # xs[b] holds this step's input
+    scanned = [ev() for _ in VARIANTS]
+    copied = [ev() for _ in VARIANTS]
+    for e in x_free + copied:
+        e.record(st)
+    state = {"k": 0}
 
     def step():
-        with torch.cuda.stream(st):
-            x.copy_(pin_in, non_blocking=True)
-            for i, (w, comp) in enumerate(VARIANTS):
-                s = cox.cox_tile_scan(cox.COX_SUM, cox.COX_F32, w, BLOCK, x.data_ptr(), outs[i].data_ptr(), N_ELEMS,
-                                      cox.COX_F_COMPENSATED if comp else 0, sh)
-                if s != 0:
-                    raise cox.CoxError(s, "cox_tile_scan")
-            for i in range(len(VARIANTS)):
+        b = state["k"] % 2
+        state["k"] += 1
+        s_h2d.wait_event(x_free[b])
+        with torch.cuda.stream(s_h2d):
+            xs[b].copy_(pin_in, non_blocking=True)
+        x_ready[b].record(s_h2d)
+        st.wait_event(x_ready[b])
+        for i, (w, comp) in enumerate(VARIANTS):
+            st.wait_event(copied[i])
+            s = cox.cox_tile_scan(cox.COX_SUM, cox.COX_F32, w, BLOCK, xs[b].data_ptr(), outs[i].data_ptr(), N_ELEMS,
+                                  cox.COX_F_COMPENSATED if comp else 0, sh)
+            if s != 0:
+                raise cox.CoxError(s, "cox_tile_scan")
+            scanned[i].record(st)
+        x_free[b].record(st)
+        for i in range(len(VARIANTS)):
+            s_d2h.wait_event(scanned[i])
+            with torch.cuda.stream(s_d2h):
                 pin_out[i].copy_(outs[i], non_blocking=True)
+            copied[i].record(s_d2h)
 
     for _ in range(2):
         step()
-    st.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(st)
+    s_h2d.wait_event(a)
+    s_d2h.wait_event(a)
     for _ in range(K):
         step()
-    b.record(st)
-    b.synchronize()
-    ms = a.elapsed_time(b) / K
+    for e in copied:
+        st.wait_event(e)
+    z.record(st)
+    z.synchronize()
+    ms = a.elapsed_time(z) / K
     return {"value": round(BYTES_PER_LAUNCH * len(VARIANTS) / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "ms_per_step": round(ms, 4), "steps": K, "h2d_bytes_per_step": N_ELEMS * 4,
-            "d2h_bytes_per_step": N_ELEMS * 4 * len(VARIANTS)}
+            "d2h_bytes_per_step": N_ELEMS * 4 * len(VARIANTS),
+            "pipelining": "input copy, scans and output copies on three streams, ordered by events"}
 
 
 def _time_launches(st, fn, iters=20, warm=3):
@@ -315,6 +347,35 @@ def run_secondary(dev, st):
     ms = _time_launches(st, lambda: chk(cox.cox_tile_reduce(0, 0, 32, 256, 1, x.data_ptr(), out.data_ptr(), 16384, 0,
                                                             None, None, 0, sh)), iters=200)
     res["block_sum_64x256_int32"] = {"us_per_call": round(ms * 1e3, 2)}
+
+    # tile reduce of 2^26 fp32 (one result per tile; compensated with its low word)
+    n = 1 << 26
+    f = torch.from_numpy(inputs.normal_f32(n, inputs.BASE_SEED + 1)).to(dev)
+    tr = {}
+    for W in (2, 32):
+        y = torch.empty(n // W, dtype=torch.float32, device=dev)
+        ylo = torch.empty(n // W, dtype=torch.float32, device=dev)
+        for comp in (False, True):
+            ms = _time_launches(st, lambda: chk(cox.cox_tile_reduce(0, 2, W, 256, 0, f.data_ptr(), y.data_ptr(), n,
+                                                                    1 if comp else 0,
+                                                                    ylo.data_ptr() if comp else None, None, 0, sh)))
+            gbs = (n * 4 + (n // W) * 4 * (2 if comp else 1)) / (ms * 1e-3) / 1e9
+            tr[f"W{W}{'_comp' if comp else '_plain'}"] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1),
+                                                         "frac": round(gbs / peak, 3)}
+        del y, ylo
+    res["tile_reduce_2p26_fp32"] = tr
+    br = {}
+    for B in (256, 1024):
+        y = torch.empty(n // B, dtype=torch.float32, device=dev)
+        for comp in (False, True):
+            ms = _time_launches(st, lambda: chk(cox.cox_tile_reduce(0, 2, 32, B, 1, f.data_ptr(), y.data_ptr(), n,
+                                                                    1 if comp else 0, None, None, 0, sh)))
+            gbs = (n * 4 + (n // B) * 4) / (ms * 1e-3) / 1e9
+            br[f"B{B}{'_comp' if comp else '_plain'}"] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1),
+                                                         "frac": round(gbs / peak, 3)}
+        del y
+    res["block_reduce_2p26_fp32_W32"] = br
+    del f
 
     # stable compaction of 2^28 int32 keys at densities 0.1/0.5/0.9
     n = 1 << 28
@@ -683,7 +744,7 @@ def run_profile(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cox", choices=["cox", "reference"])
     ap.add_argument("--no-secondary", action="store_true")

@@ -473,6 +473,86 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// --------------------------------------------------- per-warp row ring
+// Streams chunks of 32 rows x 32 elements (4 KB) of a tensor map built by
+// encode_rows32_map (box 32 x 32) through a ring of kRingStages buffers per
+// warp, two chunks in flight while one is processed.  Warp `gw` of `nw` takes
+// chunks gw, gw + nw, ...; for each, lane 0 has armed the slot's mbarrier and
+// issued the 2D TMA load, every lane waits (bounded), then
+//   body(c, buf)  reads the chunk (row r at uint4 r*8, its unit j at unit
+//                 j ^ (r & 7)) and, when STORE, leaves its results there;
+// with STORE the ring writes the buffer back through `tout` by TMA store and
+// refills a slot only after the previous store has read it.  Chunks past the
+// tensor's last row read as 0 and are not stored.  A load that does not land
+// within `limit` polls records kDevTimeout, gives the copies in flight a
+// bounded wait and ends the warp's loop.  CTAs are kRingWarps warps.
+constexpr int kRingStages = 3;
+constexpr int kRingWarps = 8;
+constexpr uint32_t kRingChunkBytes = 32 * 32 * 4;
+constexpr size_t kRingSmem = (size_t)kRingWarps * kRingStages * kRingChunkBytes + 1024 + kRingWarps * kRingStages * 8;
+
+template <bool STORE, class Body>
+__device__ __forceinline__ void row_ring(const CUtensorMap* tin, const CUtensorMap* tout, int64_t nch, uint32_t limit,
+                                         unsigned* status, Body&& body) {
+  extern __shared__ uint8_t ring_smem_raw[];
+  uint8_t* base =
+      reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ring_smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* ring = base + (size_t)warp * kRingStages * kRingChunkBytes;
+  uint64_t* bars =
+      reinterpret_cast<uint64_t*>(base + (size_t)kRingWarps * kRingStages * kRingChunkBytes) + warp * kRingStages;
+  const int64_t gw = (int64_t)blockIdx.x * kRingWarps + warp, nw = (int64_t)gridDim.x * kRingWarps;
+  if (lane == 0) {
+    for (int k = 0; k < kRingStages; ++k) mbar_init(bars + k, 1);
+    mbar_init_fence();
+    for (int k = 0; k < kRingStages - 1; ++k) {
+      const int64_t c = gw + k * nw;
+      if (c < nch) {
+        mbar_arrive_expect_tx(bars + k, kRingChunkBytes);
+        tma_load_2d(ring + k * kRingChunkBytes, tin, 0, (int)(c * 32), bars + k);
+      }
+    }
+  }
+  __syncwarp();
+  bool ok = true;
+  int64_t k = 0;
+  for (int64_t c = gw; c < nch; c += nw, ++k) {
+    const int slot = (int)(k % kRingStages);
+    uint4* buf = reinterpret_cast<uint4*>(ring + slot * kRingChunkBytes);
+    ok = mbar_wait_bounded(bars + slot, (uint32_t)((k / kRingStages) & 1), limit);
+    if (!__all_sync(kFull, ok)) {
+      ok = false;
+      break;
+    }
+    body(c, buf);
+    fence_proxy_async_smem();  // this lane's accesses to the buffer, before the async proxy's
+    __syncwarp();
+    if (lane == 0) {
+      if constexpr (STORE) tma_store_2d(tout, 0, (int)(c * 32), buf);
+      const int64_t cn = c + (kRingStages - 1) * nw;  // refill the previous chunk's slot
+      if (cn < nch) {
+        const int ns = (int)((k + kRingStages - 1) % kRingStages);
+        if constexpr (STORE) tma_store_wait_read1();  // the previous chunk's store has read it
+        mbar_arrive_expect_tx(bars + ns, kRingChunkBytes);
+        tma_load_2d(ring + ns * kRingChunkBytes, tin, 0, (int)(cn * 32), bars + ns);
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (!ok) {
+      atomicOr(status, 1u);  // kDevTimeout
+      for (int j = 0; j < kRingStages - 1; ++j) {
+        const int64_t kk = k + j;
+        if (gw + kk * nw < nch)
+          mbar_wait_bounded(bars + (int)(kk % kRingStages), (uint32_t)((kk / kRingStages) & 1), limit);
+      }
+    }
+    if constexpr (STORE) tma_store_wait_all();
+  }
+  __syncwarp();
+}
+
 // ------------------------------------------------------------ host helpers
 // Tensor map of a 32-bit array viewed as `rows` rows of 32 elements (128 B),
 // boxes of 32 x `box_rows`, 128-byte swizzle: in shared memory the 16-byte

@@ -56,6 +56,102 @@ __global__ void __launch_bounds__(1024) k_reduce_tile(const uint32_t* __restrict
   }
 }
 
+// ------------------------------------------- TILE scope, one row per lane
+// Code 1's tree with each width-W tile collapsed into one thread (the
+// paper's intra-warp loop): for offset = W/2 .. 1, x[i] = x[i] op x[i + offset]
+// for i < offset -- the operands the rank-i lane combines in the shuffle form
+// (lanes at or past the offset only compute values that rank 0 never reads).
+// Same combines, same order, same bits.
+template <class R, int W>
+__device__ __forceinline__ void reduce_row_regs(typename R::V (&v)[32]) {
+#pragma unroll
+  for (int t0 = 0; t0 < 32; t0 += W)
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1)
+#pragma unroll
+      for (int i = 0; i < off; ++i) v[t0 + i] = R::op(v[t0 + i], v[t0 + i + off]);
+}
+
+// Writes the 32 / W tile results of one row (tiles t0 .. t0 + 32/W - 1);
+// used for the partial last row.
+template <class R, int W>
+__device__ __forceinline__ void reduce_row_out(const typename R::V (&v)[32], int64_t t0, int64_t ntiles,
+                                               uint32_t* __restrict__ out, float* __restrict__ lo) {
+  constexpr int NT = 32 / W;
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    if (t0 + j < ntiles) {
+      out[t0 + j] = to_bits(R::out(v[j * W]));
+      if (lo) lo[t0 + j] = R::lo(v[j * W]);
+    }
+  }
+}
+
+// Writes the chunk's results (lane t's NT values at shared word t*P + j, P =
+// NT + 1 for NT > 1 so that the 32 lanes' writes hit 32 banks) to dst[0 ..
+// cnt) in tile order with coalesced warp stores.
+template <int NT>
+__device__ __forceinline__ void copy_out_padded(const uint32_t* so, uint32_t* __restrict__ dst, int cnt, int lane) {
+  constexpr int P = NT > 1 ? NT + 1 : 1;
+  for (int e = lane; e < cnt; e += 32) dst[e] = so[(e / NT) * P + (e % NT)];
+}
+
+// Persistent warps stream chunks of 32 rows through row_ring (load only);
+// lane t reduces row t's NT = 32 / W tiles in registers.  The chunk's
+// 32 x NT results (tiles (32c + t) NT + j, contiguous) are staged in the
+// chunk's own buffer -- free once every lane holds its row -- and leave by
+// coalesced warp stores; then the low words the same way.  The last n % 32 elements (a
+// partial row, padded) go to thread 0 of CTA 0.
+template <class R, int W>
+__global__ void __launch_bounds__(kRingWarps * 32, 2)
+    k_reduce_tile_rows(const __grid_constant__ CUtensorMap tin, const uint32_t* __restrict__ in,
+                       uint32_t* __restrict__ out, float* __restrict__ lo, int64_t n, uint32_t limit,
+                       unsigned* status) {
+  using T = typename R::T;
+  using V = typename R::V;
+  constexpr int NT = 32 / W;
+  const int lane = threadIdx.x & 31;
+  const int64_t rows = n / 32;
+  const int64_t ntiles = (n + W - 1) / W;
+  row_ring<false>(&tin, nullptr, (rows + 31) / 32, limit, status, [&](int64_t c, uint4* buf) {
+    V v[32];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint4 q = buf[lane * 8 + (j ^ (lane & 7))];
+      v[4 * j] = R::load(from_bits<T>(q.x));
+      v[4 * j + 1] = R::load(from_bits<T>(q.y));
+      v[4 * j + 2] = R::load(from_bits<T>(q.z));
+      v[4 * j + 3] = R::load(from_bits<T>(q.w));
+    }
+    reduce_row_regs<R, W>(v);
+    __syncwarp();  // every lane holds its row: the buffer is free for the results
+    constexpr int P = NT > 1 ? NT + 1 : 1;
+    uint32_t* so = reinterpret_cast<uint32_t*>(buf);
+    const int64_t r0 = c * 32;
+    const int valid = (int)((rows - r0 < 32 ? rows - r0 : 32) * NT);  // rows past the end are not written
+#pragma unroll
+    for (int j = 0; j < NT; ++j) so[lane * P + j] = to_bits(R::out(v[j * W]));
+    __syncwarp();
+    copy_out_padded<NT>(so, out + r0 * NT, valid, lane);
+    if (lo) {
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < NT; ++j) so[lane * P + j] = __float_as_uint(R::lo(v[j * W]));
+      __syncwarp();
+      copy_out_padded<NT>(so, reinterpret_cast<uint32_t*>(lo) + r0 * NT, valid, lane);
+    }
+  });
+  if (blockIdx.x == 0 && threadIdx.x == 0 && rows * 32 < n) {
+    const int64_t b = rows * 32;
+    const int m = (int)(n - b);
+    V v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = R::load(i < m ? from_bits<T>(in[b + i]) : R::pad());
+    reduce_row_regs<R, W>(v);
+    reduce_row_out<R, W>(v, rows * NT, ntiles, out, lo);
+  }
+}
+
 // -------------------------------------------- BLOCK scope, one CTA per block
 // The CUDA-shaped kernel (Code 1 inside an SDK-style block reduction): the
 // CTA is the logical block.  Used when the grid is small (e.g. 64 blocks).
@@ -268,6 +364,23 @@ static cox_status launch_reduce(cox_scope scope, const void* d_in, void* d_out, 
   uint32_t* out = static_cast<uint32_t*>(d_out);
   const int vec = aligned16(d_in);
   using V = typename R::V;
+  if (scope == COX_SCOPE_TILE && n >= 32 && n / 32 < (int64_t(1) << 31) && aligned16(d_in)) {
+    // Aligned arrays of at least one full row: the row-per-lane kernel.
+    const int64_t rows = n / 32;
+    CUtensorMap tin;
+    if (!encode_rows32_map(&tin, d_in, rows, 32)) return COX_ECUDA;
+    auto k = k_reduce_tile_rows<R, W>;
+    static int gmax_rows;
+    if (gmax_rows == 0) {
+      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmem) != cudaSuccess)
+        return COX_ECUDA;
+      gmax_rows = persistent_grid(k, kRingWarps * 32, kRingSmem, 1 << 30);
+    }
+    const int64_t ctas = ((rows + 31) / 32 + kRingWarps - 1) / kRingWarps;
+    k<<<(int)(ctas < gmax_rows ? ctas : gmax_rows), kRingWarps * 32, kRingSmem, st>>>(
+        tin, in, out, d_lo, n, spin_limit(), device_status_word());
+    return launch_status();
+  }
   if (scope == COX_SCOPE_TILE) {
     auto k = k_reduce_tile<R, W, kRedRows>;
     const int block = 256;

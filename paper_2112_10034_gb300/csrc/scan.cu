@@ -54,55 +54,20 @@ __device__ __forceinline__ void scan_row_regs(typename R::V (&v)[32]) {
   }
 }
 
-constexpr int kRowStages = 3;                          // per-warp ring of chunk buffers
-constexpr int kRowWarps = 8;                           // 256-thread CTAs
-constexpr uint32_t kRowChunkBytes = 32 * 32 * 4;       // 32 rows of 128 B
-constexpr size_t kRowSmem = (size_t)kRowWarps * kRowStages * kRowChunkBytes + 1024 + kRowWarps * kRowStages * 8;
-
-// Persistent warps over chunks of 32 rows.  Each warp keeps two chunks in
-// flight by 2D TMA (128-byte swizzle) in a 3-stage ring; a chunk is read row
-// per lane, scanned in registers, written back in place and leaves by TMA
-// store, whose read of the buffer is awaited before the buffer is refilled.
-// `rows` = full 32-element rows (>= 1); the n - 32 rows tail elements are
-// scanned by warp 0 of CTA 0 from global memory.
+// Persistent warps stream chunks of 32 rows through row_ring: a chunk is
+// read row per lane, scanned in registers, written back in place and stored
+// by TMA.  `n / 32` full rows go through the tensor maps (>= 1 row); the last
+// n % 32 elements are scanned by thread 0 of CTA 0 from global memory.
 template <class R, int W>
-__global__ void __launch_bounds__(kRowWarps * 32, 2)
+__global__ void __launch_bounds__(kRingWarps * 32, 2)
     k_tile_scan_rows(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
                      const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n, uint32_t limit,
                      unsigned* status) {
   using T = typename R::T;
   using V = typename R::V;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint8_t* ring = base + (size_t)warp * kRowStages * kRowChunkBytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + (size_t)kRowWarps * kRowStages * kRowChunkBytes) +
-                   warp * kRowStages;
+  const int lane = threadIdx.x & 31;
   const int64_t rows = n / 32;
-  const int64_t nch = (rows + 31) / 32;
-  const int64_t gw = (int64_t)blockIdx.x * kRowWarps + warp, nw = (int64_t)gridDim.x * kRowWarps;
-  if (lane == 0) {
-    for (int k = 0; k < kRowStages; ++k) mbar_init(bars + k, 1);
-    mbar_init_fence();
-    for (int k = 0; k < kRowStages - 1; ++k) {  // prologue: the first two chunks
-      const int64_t c = gw + k * nw;
-      if (c < nch) {
-        mbar_arrive_expect_tx(bars + k, kRowChunkBytes);
-        tma_load_2d(ring + k * kRowChunkBytes, &tin, 0, (int)(c * 32), bars + k);
-      }
-    }
-  }
-  __syncwarp();
-  bool ok = true;
-  int64_t k = 0;
-  for (int64_t c = gw; c < nch; c += nw, ++k) {
-    const int slot = (int)(k % kRowStages);
-    uint4* buf = reinterpret_cast<uint4*>(ring + slot * kRowChunkBytes);
-    ok = mbar_wait_bounded(bars + slot, (uint32_t)((k / kRowStages) & 1), limit);
-    if (!__all_sync(kFull, ok)) {
-      ok = false;
-      break;
-    }
+  row_ring<true>(&tin, &tout, (rows + 31) / 32, limit, status, [&](int64_t, uint4* buf) {
     V v[32];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {  // unit j of row `lane` sits at unit j ^ (lane & 7)
@@ -117,31 +82,8 @@ __global__ void __launch_bounds__(kRowWarps * 32, 2)
     for (int j = 0; j < 8; ++j)
       buf[lane * 8 + (j ^ (lane & 7))] = make_uint4(to_bits(R::out(v[4 * j])), to_bits(R::out(v[4 * j + 1])),
                                                     to_bits(R::out(v[4 * j + 2])), to_bits(R::out(v[4 * j + 3])));
-    fence_proxy_async_smem();  // this lane's row, before the bulk store reads it
-    __syncwarp();
-    if (lane == 0) {
-      tma_store_2d(&tout, 0, (int)(c * 32), buf);
-      const int64_t cn = c + (kRowStages - 1) * nw;  // refill the slot of the previous chunk
-      if (cn < nch) {
-        const int ns = (int)((k + kRowStages - 1) % kRowStages);
-        tma_store_wait_read1();  // the previous chunk's store has read that slot
-        mbar_arrive_expect_tx(bars + ns, kRowChunkBytes);
-        tma_load_2d(ring + ns * kRowChunkBytes, &tin, 0, (int)(cn * 32), bars + ns);
-      }
-    }
-    __syncwarp();
-  }
-  if (lane == 0) {
-    if (!ok) {  // a load that did not land: record it and give the copies in flight a bounded wait
-      atomicOr(status, (unsigned)kDevTimeout);
-      for (int j = 0; j < kRowStages - 1; ++j) {
-        const int64_t kk = k + j;
-        if (gw + kk * nw < nch) mbar_wait_bounded(bars + (int)(kk % kRowStages), (uint32_t)((kk / kRowStages) & 1), limit);
-      }
-    }
-    tma_store_wait_all();  // every store has completed before the CTA ends
-  }
-  // The last n - 32 rows elements (fewer than 32): one lane, padded.
+  });
+  // The last n % 32 elements: one lane, padded.
   if (blockIdx.x == 0 && threadIdx.x == 0 && rows * 32 < n) {
     const int64_t b = rows * 32;
     const int m = (int)(n - b);
@@ -163,15 +105,15 @@ static cox_status launch_scan_rows(const void* in, void* out, int64_t n, cudaStr
   auto k = k_tile_scan_rows<R, W>;
   static int grid_cache = 0;  // persistent grid (occupancy does not change)
   if (grid_cache == 0) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmem) != cudaSuccess)
       return COX_ECUDA;
-    grid_cache = persistent_grid(k, kRowWarps * 32, kRowSmem, 1 << 30);
+    grid_cache = persistent_grid(k, kRingWarps * 32, kRingSmem, 1 << 30);
   }
   const int64_t nch = (rows + 31) / 32;
-  const int64_t ctas = (nch + kRowWarps - 1) / kRowWarps;
+  const int64_t ctas = (nch + kRingWarps - 1) / kRingWarps;
   const int grid = (int)(ctas < grid_cache ? ctas : grid_cache);
-  k<<<grid, kRowWarps * 32, kRowSmem, st>>>(tin, tout, static_cast<const uint32_t*>(in), static_cast<uint32_t*>(out),
-                                            n, spin_limit(), device_status_word());
+  k<<<grid, kRingWarps * 32, kRingSmem, st>>>(tin, tout, static_cast<const uint32_t*>(in),
+                                              static_cast<uint32_t*>(out), n, spin_limit(), device_status_word());
   return launch_status();
 }
 

@@ -183,6 +183,48 @@ def test_tile_reduce_compensated_low_word(cox, W):
     np.testing.assert_array_equal(host(lo), wlo)
 
 
+@pytest.mark.parametrize("W", WIDTHS)
+@pytest.mark.parametrize("comp", [False, True])
+def test_tile_reduce_row_path_sizes_and_alignment(cox, W, comp):
+    """Aligned inputs of >= 32 elements take the row-per-lane TMA kernel (whole
+    rows, partial chunks, a partial last row, several chunks per warp);
+    inputs offset by 4 bytes take the shuffle kernel.  Sums and low words
+    are the emulation's bits; nothing is written past the last tile."""
+    import torch
+    flags = cox.COX_F_COMPENSATED if comp else 0
+    for n in (32, 33, 1024 + 31, 32 * 45 + 7, 2432 * 1024 * 3 + 32 * 5 + 9):
+        x = inputs.normal_f32(n, seed=n + 5 * W + comp)
+        m = o.n_out(o.TILE, n, W, 256)
+        want, wlo = o.reduce_emulate(o.SUM, o.F32, W, 256, o.TILE, x, comp)
+        for off in (0, 1):
+            xd = torch.zeros(n + 8, dtype=torch.float32, device="cuda")
+            xd[off:off + n] = dev(x)
+            out = poisoned(m, torch.int32)
+            lo = poisoned(m, torch.int32)
+            assert cox.cox_tile_reduce(o.SUM, o.F32, W, 256, o.TILE, xd.data_ptr() + 4 * off, out.data_ptr(), n,
+                                       flags, lo.data_ptr() if comp else None, None, 0, None) == 0
+            got = host(out)
+            np.testing.assert_array_equal(got[:m].view(np.uint32), want.view(np.uint32))
+            assert (got[m:] == POISON).all()
+            if comp:
+                np.testing.assert_array_equal(host(lo)[:m].view(np.uint32), wlo.view(np.uint32))
+    assert cox.device_status() == cox.COX_OK
+
+
+@pytest.mark.parametrize("W", [2, 32])
+def test_tile_reduce_2p26_fp32_full_size(cox, W):
+    n = 1 << 26
+    x = inputs.normal_f32(n, seed=inputs.BASE_SEED + 2)
+    xd = dev(x)
+    for comp in (False, True):
+        got = cox.tile_reduce(xd, o.SUM, W, 256, o.TILE, compensated=comp, with_lo=comp)
+        out, lo = got if comp else (got, None)
+        want, wlo = o.reduce_emulate(o.SUM, o.F32, W, 256, o.TILE, x, comp)
+        np.testing.assert_array_equal(host(out), want)
+        if comp:
+            np.testing.assert_array_equal(host(lo), wlo)
+
+
 @pytest.mark.parametrize("dt,op", OPS)
 def test_grid_reduce(cox, dt, op):
     for n in (0, 1, 1000, 3_000_001):
