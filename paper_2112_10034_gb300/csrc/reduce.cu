@@ -13,8 +13,10 @@
 // elements per thread first (tolerance-checked for fp32) and combines the
 // per-CTA partials in CTA order in the last CTA to finish.
 #include "cox_common.cuh"
+#include "reduce_block_rows.cuh"
 
 namespace cox {
+
 
 constexpr int kRedRows = 8;
 constexpr int kGridMaxCtas = 4096;
@@ -358,8 +360,8 @@ __global__ void __launch_bounds__(1024) k_reduce_grid(const uint32_t* __restrict
 
 // ------------------------------------------------------------------ launch
 template <class R, int W>
-static cox_status launch_reduce(cox_scope scope, const void* d_in, void* d_out, float* d_lo, int64_t n,
-                                int B, unsigned flags, void* ws, size_t ws_bytes, cudaStream_t st) {
+static cox_status launch_reduce(cox_scope scope, const void* d_in, void* d_out, float* d_lo, int64_t n, int B,
+                                unsigned flags, void* ws, size_t ws_bytes, cudaStream_t st) {
   const uint32_t* in = static_cast<const uint32_t*>(d_in);
   uint32_t* out = static_cast<uint32_t*>(d_out);
   const int vec = aligned16(d_in);
@@ -402,6 +404,8 @@ static cox_status launch_reduce(cox_scope scope, const void* d_in, void* d_out, 
       k<<<(int)nblk, B, smem, st>>>(in, out, d_lo, n);
       return launch_status();
     }
+    if ((B & (B - 1)) == 0 && n >= 32 && n / 32 < (int64_t(1) << 31) && aligned16(d_in))
+      return block_rows_launch<R>(W, B, d_in, d_out, d_lo, n, st);
     auto k = k_reduce_block_warp<R, W>;
     const int block = 256;
     const int K = B >= 256 ? 1 : 256 / B;

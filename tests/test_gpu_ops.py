@@ -211,6 +211,37 @@ def test_tile_reduce_row_path_sizes_and_alignment(cox, W, comp):
     assert cox.device_status() == cox.COX_OK
 
 
+@pytest.mark.parametrize("W", [2, 8, 32])
+@pytest.mark.parametrize("B", [32, 64, 256, 1024])
+def test_block_reduce_row_path_tails_and_alignment(cox, W, B):
+    """Power-of-two blocks over aligned inputs take the row-per-lane kernel:
+    a last block made of full rows, a last block reaching into a partial row,
+    a last block shorter than one row, and inputs offset by 4 bytes (the
+    shuffle kernel).  Sums, low words and integer sums match the emulation."""
+    import torch
+    nblk = 4 * 152 + 5  # past the one-CTA-per-block path
+    for n in (nblk * B, nblk * B - 32, nblk * B - 19, (nblk - 1) * B + 7):
+        x = inputs.normal_f32(n, seed=n + W + B)
+        m = o.n_out(o.BLOCK, n, W, B)
+        want, wlo = o.reduce_emulate(o.SUM, o.F32, W, B, o.BLOCK, x, True)
+        for off in (0, 1):
+            xd = torch.zeros(n + 8, dtype=torch.float32, device="cuda")
+            xd[off:off + n] = dev(x)
+            out = poisoned(m, torch.int32)
+            lo = poisoned(m, torch.int32)
+            assert cox.cox_tile_reduce(o.SUM, o.F32, W, B, o.BLOCK, xd.data_ptr() + 4 * off, out.data_ptr(), n,
+                                       cox.COX_F_COMPENSATED, lo.data_ptr(), None, 0, None) == 0
+            got = host(out)
+            np.testing.assert_array_equal(got[:m].view(np.uint32), want.view(np.uint32), err_msg=f"n={n} off={off}")
+            assert (got[m:] == POISON).all()
+            np.testing.assert_array_equal(host(lo)[:m].view(np.uint32), wlo.view(np.uint32))
+        xi = inputs.bits_u32(n, seed=n).view(np.int32)
+        for op in (o.SUM, o.MIN, o.XOR):
+            got = host(cox.tile_reduce(dev(xi), op, W, B, o.BLOCK))
+            np.testing.assert_array_equal(got, o.reduce_emulate(op, o.I32, W, B, o.BLOCK, xi)[0])
+    assert cox.device_status() == cox.COX_OK
+
+
 @pytest.mark.parametrize("W", [2, 32])
 def test_tile_reduce_2p26_fp32_full_size(cox, W):
     n = 1 << 26
@@ -223,6 +254,8 @@ def test_tile_reduce_2p26_fp32_full_size(cox, W):
         np.testing.assert_array_equal(host(out), want)
         if comp:
             np.testing.assert_array_equal(host(lo), wlo)
+        bo = cox.tile_reduce(xd, o.SUM, W, 256, o.BLOCK, compensated=comp)
+        np.testing.assert_array_equal(host(bo), o.reduce_emulate(o.SUM, o.F32, W, 256, o.BLOCK, x, comp)[0])
 
 
 @pytest.mark.parametrize("dt,op", OPS)
