@@ -7,7 +7,7 @@
  * scans, ballot-driven stable compaction and match-based histograms.  The
  * paper (arXiv 2112.10034, COX) defines these functions' semantics by running
  * CUDA kernels that use them on CPUs (Section 2.2.1 "Warp-level collectives",
- * Section 4.2 "Support warp-level functions"); this library runs them on the
+ * Section 3.2 "Support warp-level functions"); this library runs them on the
  * GPU as hand-written sm_103a kernels.
  *
  * Conventions for every call below:

@@ -9,8 +9,8 @@ Thin numpy wrapper over ``liboracle.so`` (built from ``cox_oracle.cpp`` by
 ``oracle/build.py``), a collapsed-loop executor of CUDA warp-function
 semantics: inter-warp loops around intra-warp loops over per-lane register
 arrays, each warp function a write phase and a read phase on an exchange array
-(Sections 2.3, 4.2 and 4.6 of the paper), one CUDA block per task on a CPU
-thread pool (Section 5).  Each function's docstring names the passage it
+(Sections 2.3, 3.2 and 3.6 of the paper), one CUDA block per task on a CPU
+thread pool (Section 4).  Each function's docstring names the passage it
 follows; the C source carries the details.
 
 Codes (this package's own numbering, equal by value to the library's ABI):
@@ -100,7 +100,7 @@ def threads() -> int:
 
 
 def debug_fuse_phases(on: bool) -> None:
-    """Planted-mistake switch: drop the RAW/WAR warp barriers of Section 4.2."""
+    """Planted-mistake switch: drop the RAW/WAR warp barriers of Section 3.2."""
     _load().oracle_debug_fuse_phases(1 if on else 0)
 
 
@@ -128,7 +128,7 @@ def code1(block_dim: int, mode: int = 0) -> np.ndarray:
 
 
 def code4(block_dim: int) -> np.ndarray:
-    """Code 4 (Section 4.1): result[tx] = __all_sync(-1, tx % 2)."""
+    """Code 4 (Section 3.1): result[tx] = __all_sync(-1, tx % 2)."""
     out = np.zeros(block_dim, np.int32)
     _check(_load().oracle_code4(block_dim, _ptr(out)), "code4")
     return out

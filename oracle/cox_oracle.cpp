@@ -8,18 +8,18 @@
  *
  * What it is.  A plain, slow executor of CUDA warp-level function semantics on
  * CPU threads, built the way the paper collapses a CUDA block for a CPU
- * (Section 2.3, "hierarchical collapsing", Code 3; Section 4.6):
+ * (Section 2.3, "hierarchical collapsing", Code 3; Section 3.6):
  *   - an inter-warp loop over warp ids (`wid`) wraps intra-warp loops over the
  *     32 lanes (`tx`);
- *   - per-lane registers are arrays replicated over the block (Section 4.6);
+ *   - per-lane registers are arrays replicated over the block (Section 3.6);
  *   - every warp function is a write phase, in which each lane stores its
  *     operand into an exchange array held by the CPU thread running the block
- *     (Section 4.2), followed by a read phase in which each lane computes its
+ *     (Section 3.2), followed by a read phase in which each lane computes its
  *     result from that array; the two loops are the implicit warp barriers for
- *     the RAW and WAR hazards of Section 4.2 (Code 5);
+ *     the RAW and WAR hazards of Section 3.2 (Code 5);
  *   - a block barrier ends an inter-warp loop; work done by one warp only is
  *     guarded by the warp-uniform flag of its lane 0 (loop peeling, Section 2.3);
- *   - blocks run one per task on a pool of CPU threads (Section 5).
+ *   - blocks run one per task on a pool of CPU threads (Section 4).
  *
  * Warp-function semantics are those of the public PTX `shfl.sync`, `vote.sync`
  * and `match.sync` definitions, which the paper defers to (Section 2.2.1).
@@ -74,7 +74,7 @@ int pool_threads() {
   return h ? (int)h : 1;
 }
 
-// Section 5: the runtime maps one CUDA block to one CPU thread; a thread pool
+// Section 4: the runtime maps one CUDA block to one CPU thread; a thread pool
 // (named there as the natural optimisation of fork/join) runs the grid.
 template <class Fn>
 void launch_grid(int64_t grid, Fn&& fn) {
@@ -104,15 +104,15 @@ bool valid_block(int b) { return b >= 32 && b <= 1024 && b % 32 == 0; }
 inline float as_f(uint32_t u) { float f; std::memcpy(&f, &u, 4); return f; }
 inline uint32_t as_u(float f) { uint32_t u; std::memcpy(&u, &f, 4); return u; }
 
-// ------------------------------------------------- Section 4.2: exchange array
+// ------------------------------------------------- Section 3.2: exchange array
 // The array every warp function goes through.  It lives in the memory of the
 // CPU thread that runs the block, so blocks running on different CPU threads
-// never race on it (Section 4.2).
+// never race on it (Section 3.2).
 thread_local uint32_t warp_xchg[32];
 
 // Debug switch for the planted-mistake test: when set, warp functions fuse the
 // write and read phases into one lane loop, i.e. drop the RAW barrier of
-// Section 4.2.  Off in every normal call.
+// Section 3.2.  Off in every normal call.
 bool g_fuse_phases = false;
 
 // Source lane of shfl.sync for mode `fn` at width W (segment mask 32-W, clamp
@@ -270,7 +270,7 @@ struct Neumaier {
 // cox_shfl: element i is the operand of global thread i.
 void shfl_block(int64_t blk, int fn, int dt, int W, int B, const uint32_t* in,
                 uint32_t* out, int64_t n, int param) {
-  std::vector<uint32_t> v(B), r(B);  // replicated registers (Section 4.6)
+  std::vector<uint32_t> v(B), r(B);  // replicated registers (Section 3.6)
   bool pred[32], valid[32];
   for (int wid = 0; wid < B / 32; ++wid) {  // inter-warp loop
     uint32_t* vw = &v[wid * 32];
@@ -529,7 +529,7 @@ int oracle_code4(int B, int32_t* out) {
   return ST_OK;
 }
 
-// Two consecutive votes through the one exchange array (Section 4.2, Code 5):
+// Two consecutive votes through the one exchange array (Section 3.2, Code 5):
 // first all(tx % 2), then all(1).  out[2*t] and out[2*t+1] are thread t's two
 // results.
 int oracle_vote_pair(int B, int32_t* out) {

@@ -35,12 +35,13 @@ __global__ void __launch_bounds__(R::kComp ? 256 : 1024) k_tile_scan(const uint3
 
 // ------------------------------------------------ one tile row per lane
 // The same Hillis-Steele combines with each width-W tile collapsed into one
-// thread -- the paper's intra-warp loop (Section 3), applied on the GPU: lane
-// t of a warp holds row t (32 consecutive elements, 32/W tiles) of the warp's
-// 1024-element chunk, and step d sets x[i] = x[i-d] op x[i] for rank i from
-// W-1 down to d, so x[i-d] still holds the previous step's value, exactly as
-// the shuffle's source lane does.  Same operands in the same order, hence the
-// same bits, with no shuffles, selects or idle lanes.
+// thread -- the paper's intra-warp loop (Section 2.3, Code 3), applied on
+// the GPU: lane t of a warp holds row t (32 consecutive elements, 32/W
+// tiles) of the warp's 1024-element chunk, and step d sets
+// x[i] = x[i-d] op x[i] for rank i from W-1 down to d, so x[i-d] still holds
+// the previous step's value, exactly as the shuffle's source lane does.
+// Same operands in the same order, hence the same bits, with no shuffles,
+// selects or idle lanes.
 template <class R, int W>
 __device__ __forceinline__ void scan_row_regs(typename R::V (&v)[32]) {
 #pragma unroll

@@ -6,7 +6,7 @@ Code 4 of the paper, in tests/golden), by brute-force lane enumeration
 definition (np.add.reduceat, np.cumsum, boolean masks, np.bincount,
 math.fsum), by closed forms, or by the invariants of each op.  A planted
 mistake (the oracle's debug switch that drops the warp barriers of
-Section 4.2) must fail the paper pins.
+Section 3.2) must fail the paper pins.
 """
 import math
 import os
@@ -64,7 +64,7 @@ def test_code4_companions_ballot_and_any():
 
 
 def test_consecutive_votes_are_independent():
-    # Section 4.2 / Code 5: two votes in a row through one exchange array.
+    # Section 3.2 / Code 5: two votes in a row through one exchange array.
     r = o.vote_pair(64)
     assert (r[:, 0] == 0).all() and (r[:, 1] == 1).all()
 
