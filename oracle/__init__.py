@@ -255,3 +255,33 @@ def rel_err(y: np.ndarray, ref64: np.ndarray, abs64: np.ndarray) -> np.ndarray:
     den = np.maximum(np.abs(ref64), 2.0 ** -24 * abs64)
     den = np.where(den == 0, 1.0, den)
     return np.abs(y - ref64) / den
+
+
+# ------------------------------------------- grid-wide reduce-then-broadcast
+# The cooperative-groups grid sync that gpuConjugateGradient needs and COX
+# cannot provide (Table 1; Section 5.1): a reduction over the whole grid,
+# a grid-wide barrier, then every thread uses the result.  The oracle is the
+# plain definition of the two steps, with no barrier to model.
+GRID_SUB_MIN, GRID_NORMALIZE = 0, 1
+
+
+def grid_sub_min(dt: int, x: np.ndarray) -> np.ndarray:
+    """y_i = x_i - min_j x_j: integers wrap mod 2^32 (reading R6), fp32 is one
+    IEEE round-to-nearest subtraction of the exact minimum."""
+    if dt == F32:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        return (x - x.min()).astype(np.float32)
+    t = np.int32 if dt == I32 else np.uint32
+    x = np.ascontiguousarray(x).view(t)
+    m = np.array([x.min()], dtype=t).view(np.uint32)
+    return (x.view(np.uint32) - m).view(t)
+
+
+def grid_normalize_ref(x: np.ndarray):
+    """y_i = x_i / sqrt(sum_j x_j^2) in FP64 for fp32 x.  Squares of fp32
+    values are exact in FP64 and math.fsum rounds their sum once, so the
+    norm is the correctly rounded FP64 value.  Returns (ref64, norm64)."""
+    import math
+    x64 = np.ascontiguousarray(x, dtype=np.float32).astype(np.float64)
+    norm = math.sqrt(math.fsum((x64 * x64).tolist()))
+    return x64 / norm, norm

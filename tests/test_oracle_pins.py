@@ -424,3 +424,57 @@ def test_long_segment_scan_reference_equals_numpy(L):
         seg = f[t0:t0 + L].astype(np.float64)
         want = np.cumsum(seg)  # FP64 running sum: close to the exact prefix for these sizes
         assert np.allclose(ref[t0:t0 + L], want, rtol=0, atol=1e-9 * np.abs(seg).sum() + 1e-12)
+
+
+# ------------------------------------------- grid reduce-then-broadcast pins
+def test_grid_sub_min_integers_by_python_ints():
+    for dt, lo, hi in ((o.I32, -2**31, 2**31), (o.U32, 0, 2**32)):
+        x = inputs.bits_u32(257, seed=3 + dt)
+        x = x.view(np.int32) if dt == o.I32 else x
+        y = o.grid_sub_min(dt, x)
+        m = min(int(v) for v in x)
+        want = [((int(v) - m) % 2**32) for v in x]
+        assert [int(v) % 2**32 for v in y] == want
+        assert int(y[int(np.argmin(x))]) == 0  # the minimum's lane gets 0
+    # a constant array maps to zeros; the wrap of the extremes
+    assert (o.grid_sub_min(o.I32, np.full(9, -7, np.int32)) == 0).all()
+    np.testing.assert_array_equal(o.grid_sub_min(o.I32, np.array([2**31 - 1, -2**31], np.int32)),
+                                  np.array([-1, 0], np.int32))
+
+
+def test_grid_sub_min_fp32_is_one_correct_rounding():
+    from fractions import Fraction
+    x = inputs.normal_f32(513, seed=8) * np.float32(1e3)
+    x[7] = np.float32(-0.0)
+    y = o.grid_sub_min(o.F32, x)
+    m = Fraction(float(x.min()))
+    for v, got in zip(x, y):
+        exact = Fraction(float(v)) - m
+        # the fp32 value nearest the exact difference (ties away from an odd last bit)
+        f = np.float32(float(exact))
+        if Fraction(float(f)) != exact:
+            lo, hi = sorted((f, np.nextafter(f, np.float32(np.inf) if Fraction(float(f)) < exact else
+                                             np.float32(-np.inf))), key=float)
+            dlo, dhi = exact - Fraction(float(lo)), Fraction(float(hi)) - exact
+            f = lo if dlo < dhi or (dlo == dhi and (int(lo.view(np.uint32)) & 1) == 0) else hi
+        assert float(got) == float(f)
+    assert (y >= 0).all() and y[int(np.argmin(x))] == 0
+
+
+def test_grid_normalize_closed_forms():
+    ref, norm = o.grid_normalize_ref(np.array([3, 4], np.float32))
+    assert norm == 5.0 and list(ref) == [0.6, 0.8]
+    for n in (1, 16, 1000):
+        ref, norm = o.grid_normalize_ref(np.full(n, 2.5, np.float32))
+        assert norm == pytest.approx(2.5 * math.sqrt(n), rel=1e-15)
+        assert np.allclose(ref, 1 / math.sqrt(n), rtol=1e-15)
+    x = inputs.normal_f32(4097, seed=9)
+    ref, norm = o.grid_normalize_ref(x)
+    assert math.fsum((ref * ref).tolist()) == pytest.approx(1.0, rel=1e-14)
+    assert np.all(np.sign(ref) == np.sign(x))
+    ref2, norm2 = o.grid_normalize_ref(x * np.float32(2.0 ** 20))  # power-of-two scaling is exact
+    np.testing.assert_array_equal(ref2, ref)
+    assert norm2 == norm * 2.0 ** 20
+    perm = np.random.default_rng(1).permutation(x.size)
+    ref3, _ = o.grid_normalize_ref(x[perm])
+    np.testing.assert_array_equal(ref3, ref[perm])
