@@ -438,6 +438,24 @@ def run_secondary(dev, st):
         del xs, ys
     res["grid_scan"] = gs
 
+    # grid-wide reduce-then-broadcast in one cooperative kernel (algorithmic: 4 B in + 4 B out per element)
+    gb = {}
+    for nn in (1 << 22, 1 << 26):
+        xg = torch.randn(nn, device=dev, dtype=torch.float32)
+        yg = torch.empty_like(xg)
+        wsb_g = cox.cox_grid_broadcast_workspace(nn)
+        ws_g = torch.empty(wsb_g, dtype=torch.uint8, device=dev)
+        for name, opg in (("sub_min", 0), ("normalize", 1)):
+            ms = _time_launches(st, lambda: chk(cox.cox_grid_broadcast(opg, 2, xg.data_ptr(), yg.data_ptr(), nn,
+                                                                       ws_g.data_ptr(), wsb_g, sh)))
+            gbs = nn * 8 / (ms * 1e-3) / 1e9
+            gb[f"{name}_2p{nn.bit_length() - 1}_fp32"] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1),
+                                                          "frac": round(gbs / peak, 3)}
+        del xg, yg
+    gb["note"] = ("2^22 elements stay in shared memory across the barrier (read once); 2^26 are read twice, "
+                  "so at most 8/12 of the copy peak")
+    res["grid_broadcast"] = gb
+
     # grid reduce of 2^28 fp32, compensated
     f = torch.randn(n, dtype=torch.float32, device=dev)
     r = torch.empty(1, dtype=torch.float32, device=dev)

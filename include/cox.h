@@ -182,6 +182,36 @@ cox_status cox_scan(cox_op op, cox_dtype dt, cox_scope scope, int block_dim, con
 size_t cox_scan_workspace(cox_scope scope, int64_t n);
 
 /*
+ * cox_grid_broadcast -- a reduction over the whole array, a grid-wide
+ * barrier, then every element uses the result, in ONE cooperative kernel:
+ * the grid sync of cooperative groups that gpuConjugateGradient needs and
+ * COX cannot support (Table 1; Section 5.1).
+ *   COX_GRID_SUB_MIN   y_i = x_i - min_j x_j.  I32/U32 wrap mod 2^32; F32
+ *                      subtracts (IEEE, round to nearest) the minimum in
+ *                      totalOrder (-0 below +0, NaNs ignored; all NaN
+ *                      gives NaN).  Exact: the same bits for any grid.
+ *   COX_GRID_NORMALIZE y_i = x_i / ||x||_2 (F32 only): the squares are
+ *                      summed with TwoSum pairs, the CTA partials in FP64
+ *                      in CTA order (the same total in every CTA), the
+ *                      norm rounded once to fp32, one IEEE division.  A
+ *                      zero vector gives 0/0 = NaN.
+ * d_in, d_out: n 32-bit elements, device memory (they may be the same
+ *   array).  Arrays up to ~29 MB stay in shared memory across the barrier
+ *   (read once, by TMA bulk copies, when d_in and d_out are 16-byte
+ *   aligned); larger ones are read again after it.
+ * d_workspace: cox_grid_broadcast_workspace(n) bytes, 16-byte aligned,
+ *   zeroed by the call; not shared across concurrent calls.
+ * The barrier waits are bounded (cox_set_spin_limit); one that runs out
+ * sets COX_ETIMEOUT in the device status word and the CTA writes nothing.
+ * Returns COX_EINVAL for a bad op/dtype pair, COX_ENOMEM for a short
+ * workspace, COX_ECUDA if the cooperative launch is refused.
+ */
+typedef enum { COX_GRID_SUB_MIN = 0, COX_GRID_NORMALIZE = 1 } cox_gridop;
+cox_status cox_grid_broadcast(cox_gridop op, cox_dtype dt, const void* d_in, void* d_out, int64_t n,
+                              void* d_workspace, size_t workspace_bytes, void* stream);
+size_t cox_grid_broadcast_workspace(int64_t n);
+
+/*
  * cox_ballot_compact -- stable stream compaction driven by warp ballots.
  *
  * The filter of the SDK's filter_arr (Table 1) with a static, full-warp group:

@@ -265,12 +265,27 @@ def rel_err(y: np.ndarray, ref64: np.ndarray, abs64: np.ndarray) -> np.ndarray:
 GRID_SUB_MIN, GRID_NORMALIZE = 0, 1
 
 
+def fp32_min_total_order(x: np.ndarray) -> np.float32:
+    """The minimum of fp32 values under IEEE totalOrder restricted to numbers
+    (-0 < +0), NaNs ignored; NaN if every value is NaN."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    key = np.where(u & 0x80000000, ~u, u | 0x80000000).astype(np.uint32)
+    key = np.where(np.isnan(x), np.uint32(0xFFFFFFFF), key)
+    k = key.min()
+    bits = np.uint32(~k) if not (k & 0x80000000) else np.uint32(k & 0x7FFFFFFF)
+    if k == 0xFFFFFFFF:
+        bits = np.uint32(0x7FFFFFFF)
+    return np.array([bits], np.uint32).view(np.float32)[0]
+
+
 def grid_sub_min(dt: int, x: np.ndarray) -> np.ndarray:
-    """y_i = x_i - min_j x_j: integers wrap mod 2^32 (reading R6), fp32 is one
-    IEEE round-to-nearest subtraction of the exact minimum."""
+    """y_i = x_i - min_j x_j: integers wrap mod 2^32 (reading R6); fp32 is one
+    IEEE round-to-nearest subtraction of the minimum taken in totalOrder
+    (-0 below +0, NaNs ignored; reading R18)."""
     if dt == F32:
         x = np.ascontiguousarray(x, dtype=np.float32)
-        return (x - x.min()).astype(np.float32)
+        with np.errstate(invalid="ignore"):
+            return (x - fp32_min_total_order(x)).astype(np.float32)
     t = np.int32 if dt == I32 else np.uint32
     x = np.ascontiguousarray(x).view(t)
     m = np.array([x.min()], dtype=t).view(np.uint32)

@@ -22,6 +22,7 @@ COX_SUM, COX_MIN, COX_MAX, COX_AND, COX_OR, COX_XOR = range(6)
 (COX_SHFL_IDX, COX_SHFL_UP, COX_SHFL_DOWN, COX_SHFL_XOR,
  COX_BALLOT, COX_ANY, COX_ALL, COX_MATCH_ANY) = range(8)
 COX_SCOPE_TILE, COX_SCOPE_BLOCK, COX_SCOPE_GRID = 0, 1, 2
+COX_GRID_SUB_MIN, COX_GRID_NORMALIZE = 0, 1
 COX_F_COMPENSATED, COX_F_FP64_COMBINE, COX_F_WS_READY, COX_F_NATIVE_MATCH, COX_F_DIRECT_ATOMICS = 1, 2, 4, 8, 16
 FULL_MASK = 0xFFFFFFFF
 
@@ -41,6 +42,8 @@ SIGNATURES = {
     "cox_tile_scan": (_I, [_I, _I, _I, _I, _P, _P, _I64, _U, _P]),
     "cox_scan": (_I, [_I, _I, _I, _I, _P, _P, _I64, _U, _I, _P, _SZ, _P]),
     "cox_scan_workspace": (_SZ, [_I, _I64]),
+    "cox_grid_broadcast": (_I, [_I, _I, _P, _P, _I64, _P, _SZ, _P]),
+    "cox_grid_broadcast_workspace": (_SZ, [_I64]),
     "cox_ballot_compact": (_I, [_I, _I, _I, _P, _I64, _I64, _P, _P, _P, _SZ, _U, _P]),
     "cox_ballot_compact_workspace": (_SZ, [_I64, _I]),
     "cox_ballot_compact_static": (_I, [_I, _I, _I, _P, _I64, _I64, _P, _P, _P]),
@@ -125,6 +128,14 @@ def cox_scan(op, dt, scope, block_dim, d_in, d_out, n, flags, exclusive, d_ws, w
 
 def cox_scan_workspace(scope, n) -> int:
     return lib().cox_scan_workspace(scope, n)
+
+
+def cox_grid_broadcast(op, dt, d_in, d_out, n, d_ws, ws_bytes, stream) -> int:
+    return lib().cox_grid_broadcast(op, dt, d_in, d_out, n, d_ws, ws_bytes, stream)
+
+
+def cox_grid_broadcast_workspace(n) -> int:
+    return lib().cox_grid_broadcast_workspace(n)
 
 
 def cox_ballot_compact(dt, width, block_dim, d_keys, n, threshold, d_out, d_count, d_ws, ws_bytes, flags,
@@ -303,6 +314,20 @@ def scan(x, op: int = COX_SUM, scope: int = COX_SCOPE_GRID, block_dim: int = 256
                     COX_F_COMPENSATED if compensated else 0, 1 if exclusive else 0,
                     workspace.data_ptr() if workspace is not None else None, ws_bytes, _stream(x.device)),
            "cox_scan")
+    return out
+
+
+def grid_broadcast(x, op: int = COX_GRID_SUB_MIN, unsigned: bool = False, out=None, workspace=None):
+    """Reduce-then-broadcast in one cooperative kernel (cox_grid_broadcast)."""
+    t = _torch()
+    x = _dev_tensor(x)
+    if out is None:
+        out = t.empty_like(x)
+    ws_bytes = cox_grid_broadcast_workspace(x.numel())
+    if workspace is None:
+        workspace = t.empty(ws_bytes, dtype=t.uint8, device=x.device)
+    _check(cox_grid_broadcast(op, _dtype_code(x, unsigned), x.data_ptr(), out.data_ptr(), x.numel(),
+                              workspace.data_ptr(), ws_bytes, _stream(x.device)), "cox_grid_broadcast")
     return out
 
 

@@ -478,3 +478,17 @@ def test_grid_normalize_closed_forms():
     perm = np.random.default_rng(1).permutation(x.size)
     ref3, _ = o.grid_normalize_ref(x[perm])
     np.testing.assert_array_equal(ref3, ref[perm])
+
+
+def test_fp32_min_total_order_by_python_sort_key():
+    rng = np.random.default_rng(5)
+    pool = np.array([0.0, -0.0, 1.5, -1.5, np.inf, -np.inf, np.nan, 3e-45, -3e-45, 1e38], np.float32)
+    for _ in range(200):
+        a = rng.choice(pool, size=int(rng.integers(1, 8)))
+        nums = [float(v) for v in a if not math.isnan(float(v))]
+        m = o.fp32_min_total_order(a)
+        if not nums:
+            assert math.isnan(float(m))
+            continue
+        want = min(nums, key=lambda v: (v, 0 if math.copysign(1.0, v) < 0 else 1))
+        assert float(m) == want and math.copysign(1.0, float(m)) == math.copysign(1.0, want)
