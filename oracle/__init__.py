@@ -57,6 +57,7 @@ def _load():
         "oracle_reduce_counts": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _I64, _P]),
         "oracle_reduce_ref": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _I64, _P, _I64, _P, _P, _P]),
         "oracle_scan_emulate": (ctypes.c_int, [ctypes.c_int] * 5 + [_P, _P, _I64]),
+        "oracle_coalesced": (ctypes.c_int, [ctypes.c_int] * 3 + [_P, _P, _P, _I64, ctypes.c_int]),
         "oracle_scan_ref": (ctypes.c_int, [ctypes.c_int] * 3 + [_P, _I64, _P, _P, _P]),
         "oracle_ballot_compact": (ctypes.c_int, [ctypes.c_int] * 3 + [_P, _I64, _I64, _P, _P]),
         "oracle_match_histogram": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _I64, ctypes.c_int, _P, _P]),
@@ -300,3 +301,29 @@ def grid_normalize_ref(x: np.ndarray):
     x64 = np.ascontiguousarray(x, dtype=np.float32).astype(np.float64)
     norm = math.sqrt(math.fsum((x64 * x64).tolist()))
     return x64 / norm, norm
+
+
+# ------------------------------------------------ coalesced groups (dynamic)
+CG_SIZE, CG_RANK, CG_SHFL, CG_SHFL_UP, CG_SHFL_DOWN, CG_BALLOT, CG_ANY, CG_ALL, CG_REDUCE_SUM, CG_SCAN_SUM = range(10)
+
+
+def coalesced(fn: int, dt: int, block_dim: int, x: np.ndarray, active: np.ndarray, param: int = 0) -> np.ndarray:
+    """Warp functions over coalesced_threads() groups (Section 2.2.2's dynamic
+    groups; Section 2.2.3's runtime masks): the group of a warp is its lanes
+    with active != 0, in lane order.  Returns (out, written): out[i] for the
+    active lanes; written marks them (inactive lanes get no result)."""
+    xb = _bits(x)
+    act = np.ascontiguousarray(active, dtype=np.int32)
+    out = np.zeros(xb.size, np.uint32)
+    _check(_load().oracle_coalesced(fn, dt, block_dim, _ptr(xb), _ptr(act), _ptr(out), xb.size, param),
+           "coalesced")
+    return out, act != 0
+
+
+def filter_multiset(dt: int, keys: np.ndarray, threshold: int):
+    """The keys an unordered filter keeps (key < threshold in the keys' own
+    signedness; threshold clamped to the key range, reading R11), sorted, and
+    their count: what filter_arr's aggregated-atomic output holds in some order."""
+    k = np.ascontiguousarray(keys).view(np.int32 if dt == I32 else np.uint32).astype(np.int64)
+    kept = np.sort(k[k < threshold])
+    return kept, int(kept.size)

@@ -461,10 +461,91 @@ void scan_block(int64_t blk, int op, int dt, int W, int B, bool comp,
   }
 }
 
+// ------------------------------------------ coalesced groups (dynamic masks)
+// The dynamic group of Section 2.2.2 (coalesced_threads(): every active
+// thread of the warp at the call) and the runtime member masks of Section
+// 2.2.3, which COX leaves unsupported.  A lane is active when its element
+// exists (gi < n) and active[gi] != 0; the group is the warp's active lanes
+// in lane order, rank = number of active lanes below, size = their count.
+// Write phase: every active lane puts its operand into the exchange array;
+// read phase: every active lane takes its result from it by group rank.
+// Inactive lanes take no part and get no result.
+enum CgFn {
+  CG_SIZE = 0, CG_RANK = 1, CG_SHFL = 2, CG_SHFL_UP = 3, CG_SHFL_DOWN = 4,
+  CG_BALLOT = 5, CG_ANY = 6, CG_ALL = 7, CG_REDUCE_SUM = 8, CG_SCAN_SUM = 9
+};
+
+// Vote predicate of a 32-bit operand: nonzero (fp32: != 0.0f, reading R17).
+bool pred_of(int dt, uint32_t u) { return dt == DT_F32 ? as_f(u) != 0.0f : u != 0u; }
+
+void coalesced_block(int64_t blk, int fn, int dt, int B, const uint32_t* in, const int32_t* active,
+                     uint32_t* out, int64_t n, int param) {
+  for (int wid = 0; wid < B / 32; ++wid) {  // inter-warp loop
+    const int64_t base = blk * B + (int64_t)wid * 32;
+    bool act[32];
+    int member[32];  // member[k] = lane of group rank k
+    int rank[32];
+    int size = 0;
+    for (int tx = 0; tx < 32; ++tx) {  // intra-warp loop: who is active
+      act[tx] = base + tx < n && active[base + tx] != 0;
+      rank[tx] = size;
+      if (act[tx]) member[size++] = tx;
+    }
+    if (size == 0) continue;
+    for (int tx = 0; tx < 32; ++tx)  // write phase
+      if (act[tx]) warp_xchg[tx] = in[base + tx];
+    for (int tx = 0; tx < 32; ++tx) {  // read phase
+      if (!act[tx]) continue;
+      const int r = rank[tx];
+      uint32_t res = 0;
+      switch (fn) {
+        case CG_SIZE: res = (uint32_t)size; break;
+        case CG_RANK: res = (uint32_t)r; break;
+        case CG_SHFL: res = warp_xchg[member[param % size]]; break;
+        case CG_SHFL_UP: res = r >= param ? warp_xchg[member[r - param]] : warp_xchg[tx]; break;
+        case CG_SHFL_DOWN: res = r + param < size ? warp_xchg[member[r + param]] : warp_xchg[tx]; break;
+        case CG_BALLOT:
+          for (int k = 0; k < size; ++k)
+            if (pred_of(dt, warp_xchg[member[k]])) res |= 1u << k;
+          break;
+        case CG_ANY:
+          for (int k = 0; k < size; ++k) res |= pred_of(dt, warp_xchg[member[k]]) ? 1u : 0u;
+          break;
+        case CG_ALL:
+          res = 1u;
+          for (int k = 0; k < size; ++k) res &= pred_of(dt, warp_xchg[member[k]]) ? 1u : 0u;
+          break;
+        case CG_REDUCE_SUM:
+          for (int k = 0; k < size; ++k) res += warp_xchg[member[k]];
+          break;
+        default:  // CG_SCAN_SUM: inclusive prefix over ranks 0..r
+          for (int k = 0; k <= r; ++k) res += warp_xchg[member[k]];
+          break;
+      }
+      out[base + tx] = res;
+    }
+  }
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
 extern "C" {
+
+// Coalesced-group warp functions (see coalesced_block).  SHFL takes the
+// source rank param mod size; SHFL_UP/DOWN keep the caller's value when the
+// source rank is outside the group; BALLOT is group-local (bit k = rank k's
+// predicate); REDUCE/SCAN_SUM are integer sums mod 2^32 (I32/U32 only).
+int oracle_coalesced(int fn, int dt, int B, const uint32_t* in, const int32_t* active, uint32_t* out, int64_t n,
+                     int param) {
+  if (!valid_block(B) || n < 0 || fn < CG_SIZE || fn > CG_SCAN_SUM) return ST_EINVAL;
+  if (dt < DT_I32 || dt > DT_F32) return ST_EINVAL;
+  if ((fn == CG_REDUCE_SUM || fn == CG_SCAN_SUM) && dt == DT_F32) return ST_EINVAL;
+  if ((fn == CG_SHFL || fn == CG_SHFL_UP || fn == CG_SHFL_DOWN) && (param < 0 || param > 31)) return ST_EINVAL;
+  if (n == 0) return ST_OK;
+  launch_grid((n + B - 1) / B, [&](int64_t b) { coalesced_block(b, fn, dt, B, in, active, out, n, param); });
+  return ST_OK;
+}
 
 void oracle_set_threads(int k) { g_threads = k; }
 int oracle_threads(void) { return pool_threads(); }

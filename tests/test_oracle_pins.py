@@ -492,3 +492,67 @@ def test_fp32_min_total_order_by_python_sort_key():
             continue
         want = min(nums, key=lambda v: (v, 0 if math.copysign(1.0, v) < 0 else 1))
         assert float(m) == want and math.copysign(1.0, float(m)) == math.copysign(1.0, want)
+
+
+# ------------------------------------------------ coalesced-group pins
+def _per_warp_compacted(x, act):
+    """numpy form: each warp's active values, in lane order, via boolean masks."""
+    nw = (x.size + 31) // 32
+    for w in range(nw):
+        sl = slice(32 * w, min(32 * (w + 1), x.size))
+        a = act[sl] != 0
+        yield sl, np.flatnonzero(a), x[sl][a]
+
+
+@pytest.mark.parametrize("density", [0.0, 0.3, 0.9, 1.0])
+def test_coalesced_matches_numpy_compaction(density):
+    n = 32 * 40 + 13
+    x = inputs.bits_u32(n, seed=21).view(np.int32)
+    act = (inputs.uniform_u31(n, seed=22) < inputs.density_threshold(density)).astype(np.int32) if density < 1 else \
+        np.ones(n, np.int32)
+    outs = {fn: o.coalesced(fn, o.I32, 128, x, act, 3) for fn in range(10)}
+    for sl, lanes_, vals in _per_warp_compacted(x, act):
+        size = vals.size
+        for r, lane in enumerate(lanes_):
+            i = sl.start + lane
+            got = {fn: int(outs[fn][0][i]) for fn in outs}
+            assert all(outs[fn][1][i] for fn in outs)
+            assert got[o.CG_SIZE] == size and got[o.CG_RANK] == r
+            assert got[o.CG_SHFL] == int(vals[3 % size].view(np.uint32))
+            assert got[o.CG_SHFL_UP] == int((vals[r - 3] if r >= 3 else vals[r]).view(np.uint32))
+            assert got[o.CG_SHFL_DOWN] == int((vals[r + 3] if r + 3 < size else vals[r]).view(np.uint32))
+            preds = vals != 0
+            assert got[o.CG_BALLOT] == int(sum(1 << k for k in range(size) if preds[k]))
+            assert got[o.CG_ANY] == int(preds.any()) and got[o.CG_ALL] == int(preds.all())
+            assert got[o.CG_REDUCE_SUM] == int(vals.astype(np.int64).sum()) % 2**32
+            assert got[o.CG_SCAN_SUM] == int(np.cumsum(vals.astype(np.int64))[r]) % 2**32
+        inactive = np.setdiff1d(np.arange(sl.stop - sl.start), lanes_) + sl.start
+        assert not outs[o.CG_SIZE][1][inactive].any()
+
+
+def test_coalesced_full_warp_is_the_warp_function():
+    # every lane active: the coalesced group is the warp, so its functions are
+    # the width-32 warp functions already pinned (shfl, ballot, tile reduce/scan)
+    n = 32 * 16
+    x = inputs.bits_u32(n, seed=23).view(np.int32)
+    act = np.ones(n, np.int32)
+    for fn, ref in ((o.CG_SHFL, o.shfl(o.SHFL_IDX, o.I32, 32, 256, x, 5)),
+                    (o.CG_SHFL_UP, o.shfl(o.SHFL_UP, o.I32, 32, 256, x, 5)),
+                    (o.CG_SHFL_DOWN, o.shfl(o.SHFL_DOWN, o.I32, 32, 256, x, 5)),
+                    (o.CG_BALLOT, o.shfl(o.BALLOT, o.I32, 32, 256, x, 0))):
+        np.testing.assert_array_equal(o.coalesced(fn, o.I32, 256, x, act, 5)[0], ref.view(np.uint32))
+    sums, _, _ = o.reduce_ref(o.SUM, o.I32, 32, x)
+    np.testing.assert_array_equal(o.coalesced(o.CG_REDUCE_SUM, o.I32, 256, x, act)[0].view(np.int32),
+                                  np.repeat(sums.view(np.int32), 32))
+    np.testing.assert_array_equal(o.coalesced(o.CG_SCAN_SUM, o.I32, 256, x, act)[0],
+                                  o.scan_emulate(o.SUM, o.I32, 32, 256, x).view(np.uint32))
+
+
+def test_filter_multiset_equals_sorted_stable_compaction():
+    keys = inputs.uniform_u31(20_000, seed=24).view(np.int32)
+    for d in (0.0, 0.25, 1.0):
+        t = inputs.density_threshold(d)
+        kept, cnt = o.filter_multiset(o.I32, keys, t)
+        stable, scnt = o.ballot_compact(o.I32, 32, 256, keys, t)
+        assert cnt == scnt
+        np.testing.assert_array_equal(kept, np.sort(stable.astype(np.int64)))
