@@ -420,6 +420,31 @@ def run_secondary(dev, st):
     res["match_histogram_2p28_zipf"] = hres
     del z
 
+    # dynamic groups: filter_arr's aggregated atomic at d = 0.5 (2^28 keys) and a
+    # coalesced-group inclusive scan over half-active warps (2^26 elements)
+    t = inputs.density_threshold(0.5)
+    ka = torch.from_numpy(inputs.uniform_u31(n, inputs.BASE_SEED + 2)).to(dev)
+    oa = torch.empty(n, dtype=torch.int32, device=dev)
+    ca = torch.empty(1, dtype=torch.int64, device=dev)
+    ms = _time_launches(st, lambda: chk(cox.cox_filter_aggregated(0, ka.data_ptr(), n, t, oa.data_ptr(),
+                                                                  ca.data_ptr(), sh)))
+    gbs = (n * 4 + int(ca.item()) * 4) / (ms * 1e-3) / 1e9
+    dyn = {"filter_aggregated_2p28_d0.5": {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1),
+                                          "frac": round(gbs / peak, 3)}}
+    del ka, oa
+    m = 1 << 26
+    xa = torch.randint(-1000, 1001, (m,), device=dev, dtype=torch.int32)
+    act = (torch.rand(m, device=dev) < 0.5).to(torch.int32)
+    ya = torch.empty_like(xa)
+    nact = int(act.sum().item())
+    for name, fn in (("coalesced_scan_sum_2p26_half_active", 9), ("coalesced_shfl_2p26_half_active", 2)):
+        ms = _time_launches(st, lambda: chk(cox.cox_coalesced(fn, 0, 256, xa.data_ptr(), act.data_ptr(),
+                                                              ya.data_ptr(), m, 3, sh)))
+        gbs = (m * 8 + nact * 4) / (ms * 1e-3) / 1e9
+        dyn[name] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3)}
+    del xa, act, ya
+    res["dynamic_groups"] = dyn
+
     res["batched_10000_uneven"] = run_batched(dev, st)
     res["serving"] = run_serving(dev)
 

@@ -212,6 +212,48 @@ cox_status cox_grid_broadcast(cox_gridop op, cox_dtype dt, const void* d_in, voi
 size_t cox_grid_broadcast_workspace(int64_t n);
 
 /*
+ * cox_coalesced -- warp functions over coalesced_threads() groups: the
+ * dynamic groups and runtime member masks that COX leaves unsupported
+ * (Sections 2.2.2-2.2.3; filter_arr's "activated thread sync", Table 1).
+ * Element i is global thread i (block_dim a multiple of 32, so a warp is
+ * elements 32w .. 32w+31).  A lane is active when i < n and d_active[i] != 0;
+ * a warp's group is its active lanes in lane order, rank = active lanes
+ * below, size = their count.  For every active lane:
+ *   COX_CG_SIZE / COX_CG_RANK      size / rank
+ *   COX_CG_SHFL (param)            the value of group rank param mod size
+ *   COX_CG_SHFL_UP / _DOWN (param) the value of rank -/+ param, or the
+ *                                  caller's own when that rank is outside
+ *   COX_CG_BALLOT                  group-local mask: bit k = rank k's
+ *                                  predicate (value != 0; fp32 != 0.0f)
+ *   COX_CG_ANY / COX_CG_ALL        0 or 1 over the group's predicates
+ *   COX_CG_REDUCE_SUM / _SCAN_SUM  group sum / inclusive prefix by rank,
+ *                                  mod 2^32 (I32/U32 only)
+ * computed by the warp intrinsics with the group's member mask.  Inactive
+ * lanes' outputs are not written.  param in [0, 31] for the shuffles.
+ */
+typedef enum {
+  COX_CG_SIZE = 0, COX_CG_RANK = 1, COX_CG_SHFL = 2, COX_CG_SHFL_UP = 3, COX_CG_SHFL_DOWN = 4,
+  COX_CG_BALLOT = 5, COX_CG_ANY = 6, COX_CG_ALL = 7, COX_CG_REDUCE_SUM = 8, COX_CG_SCAN_SUM = 9
+} cox_cgfn;
+cox_status cox_coalesced(cox_cgfn fn, cox_dtype dt, int block_dim, const void* d_in, const int32_t* d_active,
+                         void* d_out, int64_t n, int param, void* stream);
+
+/*
+ * cox_filter_aggregated -- the SDK's filter_arr: keys with key < threshold
+ * (in the keys' signedness; threshold clamped to the key range) are written
+ * through a warp-aggregated atomic: each coalesced group of keeping lanes
+ * gets one contiguous range of d_out from an atomic add on *d_count, and a
+ * lane's slot is its group rank in it.  A warp aggregates its 16 rounds of
+ * 32 keys into one atomic.  The ORDER of the ranges is the order in which
+ * the atomics landed (not deterministic); the kept keys, their count, and
+ * the lane order inside each group are.  d_out: room for n keys; d_count:
+ * one int64, zeroed by the call, holds the count when the stream reaches
+ * the end of the call.  dt: COX_I32 or COX_U32.
+ */
+cox_status cox_filter_aggregated(cox_dtype dt, const void* d_keys, int64_t n, int64_t threshold, void* d_out,
+                                 int64_t* d_count, void* stream);
+
+/*
  * cox_ballot_compact -- stable stream compaction driven by warp ballots.
  *
  * The filter of the SDK's filter_arr (Table 1) with a static, full-warp group:

@@ -23,6 +23,8 @@ COX_SUM, COX_MIN, COX_MAX, COX_AND, COX_OR, COX_XOR = range(6)
  COX_BALLOT, COX_ANY, COX_ALL, COX_MATCH_ANY) = range(8)
 COX_SCOPE_TILE, COX_SCOPE_BLOCK, COX_SCOPE_GRID = 0, 1, 2
 COX_GRID_SUB_MIN, COX_GRID_NORMALIZE = 0, 1
+(COX_CG_SIZE, COX_CG_RANK, COX_CG_SHFL, COX_CG_SHFL_UP, COX_CG_SHFL_DOWN, COX_CG_BALLOT, COX_CG_ANY, COX_CG_ALL,
+ COX_CG_REDUCE_SUM, COX_CG_SCAN_SUM) = range(10)
 COX_F_COMPENSATED, COX_F_FP64_COMBINE, COX_F_WS_READY, COX_F_NATIVE_MATCH, COX_F_DIRECT_ATOMICS = 1, 2, 4, 8, 16
 FULL_MASK = 0xFFFFFFFF
 
@@ -44,6 +46,8 @@ SIGNATURES = {
     "cox_scan_workspace": (_SZ, [_I, _I64]),
     "cox_grid_broadcast": (_I, [_I, _I, _P, _P, _I64, _P, _SZ, _P]),
     "cox_grid_broadcast_workspace": (_SZ, [_I64]),
+    "cox_coalesced": (_I, [_I, _I, _I, _P, _P, _P, _I64, _I, _P]),
+    "cox_filter_aggregated": (_I, [_I, _P, _I64, _I64, _P, _P, _P]),
     "cox_ballot_compact": (_I, [_I, _I, _I, _P, _I64, _I64, _P, _P, _P, _SZ, _U, _P]),
     "cox_ballot_compact_workspace": (_SZ, [_I64, _I]),
     "cox_ballot_compact_static": (_I, [_I, _I, _I, _P, _I64, _I64, _P, _P, _P]),
@@ -136,6 +140,14 @@ def cox_grid_broadcast(op, dt, d_in, d_out, n, d_ws, ws_bytes, stream) -> int:
 
 def cox_grid_broadcast_workspace(n) -> int:
     return lib().cox_grid_broadcast_workspace(n)
+
+
+def cox_coalesced(fn, dt, block_dim, d_in, d_active, d_out, n, param, stream) -> int:
+    return lib().cox_coalesced(fn, dt, block_dim, d_in, d_active, d_out, n, param, stream)
+
+
+def cox_filter_aggregated(dt, d_keys, n, threshold, d_out, d_count, stream) -> int:
+    return lib().cox_filter_aggregated(dt, d_keys, n, threshold, d_out, d_count, stream)
 
 
 def cox_ballot_compact(dt, width, block_dim, d_keys, n, threshold, d_out, d_count, d_ws, ws_bytes, flags,
