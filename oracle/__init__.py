@@ -327,3 +327,34 @@ def filter_multiset(dt: int, keys: np.ndarray, threshold: int):
     k = np.ascontiguousarray(keys).view(np.int32 if dt == I32 else np.uint32).astype(np.int64)
     kept = np.sort(k[k < threshold])
     return kept, int(kept.size)
+
+
+# ------------------------------------- vote statistics and integral images
+def vote_stats(width: int, pred: np.ndarray, seg_len: int) -> np.ndarray:
+    """Batched statistics of the vote kernels (VoteAny/VoteAll, Table 1): the
+    array is cut into segments of seg_len elements (a multiple of width; the
+    last may be shorter), each segment into tiles of `width` lanes; per
+    segment: [tiles whose any() is true, tiles whose all() is true, true
+    predicates].  A ragged last tile's missing lanes are padding with a false
+    predicate (reading R5), so its all() is false.  Predicate: value != 0."""
+    p = np.ascontiguousarray(pred).view(np.int32) != 0
+    n = p.size
+    nseg = (n + seg_len - 1) // seg_len
+    out = np.zeros((nseg, 3), np.int64)
+    for s in range(nseg):
+        seg = p[s * seg_len:min(n, (s + 1) * seg_len)]
+        t = (seg.size + width - 1) // width
+        padded = np.zeros(t * width, bool)
+        padded[:seg.size] = seg
+        tiles = padded.reshape(t, width)
+        out[s] = [tiles.any(axis=1).sum(), tiles.all(axis=1).sum(), seg.sum()]
+    return out
+
+
+def integral_image(img: np.ndarray) -> np.ndarray:
+    """Integral images of a batch (B, H, W) of uint8 or 32-bit images:
+    I[b, y, x] = sum over y' <= y, x' <= x of img[b, y', x'], mod 2^32 (the
+    SDK's shfl_intimage_rows / shfl_vertical_shfl pair, Table 1, reading R6)."""
+    a = np.asarray(img)
+    a = a.astype(np.uint64) if a.dtype == np.uint8 else a.view(np.uint32).astype(np.uint64)
+    return (np.cumsum(np.cumsum(a, axis=2), axis=1) % (1 << 32)).astype(np.uint32)

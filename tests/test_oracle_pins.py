@@ -556,3 +556,49 @@ def test_filter_multiset_equals_sorted_stable_compaction():
         stable, scnt = o.ballot_compact(o.I32, 32, 256, keys, t)
         assert cnt == scnt
         np.testing.assert_array_equal(kept, np.sort(stable.astype(np.int64)))
+
+
+# ------------------------------------- vote statistics / integral image pins
+@pytest.mark.parametrize("W", WIDTHS)
+def test_vote_stats_by_ballots_of_the_pinned_vote_oracle(W):
+    # tile any/all/popcount from the oracle's own pinned ballots (bit r of the
+    # tile-local mask = rank r's predicate), summed per segment by Python loops
+    n, seg = 32 * 37 + 5, 32 * 8
+    pred = (inputs.uniform_u31(n, seed=W) < inputs.density_threshold(0.9)).astype(np.int32)
+    pred[::97] = 0
+    st = o.vote_stats(W, pred, seg)
+    ball = o.shfl(o.BALLOT, o.I32, W, 256, pred)
+    for s in range(st.shape[0]):
+        a = al = pc = 0
+        for t0 in range(s * seg, min(n, (s + 1) * seg), W):
+            m = int(ball[t0])
+            full = (1 << W) - 1
+            a += m != 0
+            al += m == full
+            pc += bin(m).count("1")
+        assert list(st[s]) == [a, al, pc]
+
+
+def test_vote_stats_closed_forms():
+    assert list(o.vote_stats(32, np.ones(64, np.int32), 64)[0]) == [2, 2, 64]
+    assert list(o.vote_stats(8, np.zeros(40, np.int32), 40)[0]) == [0, 0, 0]
+    # ragged: 3 lanes of a 4-wide tile, all true -> any but not all (padding is false)
+    assert list(o.vote_stats(4, np.ones(7, np.int32), 8)[0]) == [2, 1, 7]
+
+
+def test_integral_image_brute_force_and_closed_forms():
+    img = (inputs.bits_u32(2 * 5 * 7, seed=30) & 0xFF).astype(np.uint8).reshape(2, 5, 7)
+    got = o.integral_image(img)
+    for b in range(2):
+        for y in range(5):
+            for x in range(7):
+                assert int(got[b, y, x]) == int(img[b, :y + 1, :x + 1].astype(np.int64).sum())
+    ones = np.ones((1, 9, 13), np.uint8)
+    yy, xx = np.mgrid[0:9, 0:13]
+    np.testing.assert_array_equal(o.integral_image(ones)[0], ((yy + 1) * (xx + 1)).astype(np.uint32))
+    # the recurrence I = img + I(up) + I(left) - I(up-left), mod 2^32, on 32-bit pixels
+    big = inputs.bits_u32(3 * 11 * 17, seed=31).reshape(3, 11, 17)
+    I = o.integral_image(big).astype(np.int64)
+    im = big.astype(np.int64)
+    rec = im[:, 1:, 1:] + I[:, :-1, 1:] + I[:, 1:, :-1] - I[:, :-1, :-1]
+    np.testing.assert_array_equal(rec % 2**32, I[:, 1:, 1:])
