@@ -445,6 +445,31 @@ def run_secondary(dev, st):
     del xa, act, ya
     res["dynamic_groups"] = dyn
 
+    # second workload: batched vote statistics (2^26 predicates, 4096 segments of 16384,
+    # tiles of 32) and integral images of 64 HD frames (8-bit pixels -> 32-bit sums)
+    second = {}
+    m = 1 << 26
+    pv = (torch.rand(m, device=dev) < 0.9).to(torch.int32)
+    vs = torch.empty(3 * (m // 16384), dtype=torch.int64, device=dev)
+    ms = _time_launches(st, lambda: chk(cox.cox_vote_stats(0, 32, pv.data_ptr(), m, 16384, vs.data_ptr(), sh)))
+    gbs = m * 4 / (ms * 1e-3) / 1e9
+    second["vote_stats_2p26_w32"] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3)}
+    del pv, vs
+    B, H, W = 64, 1080, 1920
+    for name, code, bpp in (("integral_image_64x1080x1920_u8", 3, 1), ("integral_image_64x1080x1920_u32", 1, 4)):
+        img = torch.randint(0, 256, (B * H * W * bpp // 4 if bpp == 1 else B * H * W,), device=dev,
+                            dtype=torch.int32)
+        ii = torch.empty(B * H * W, dtype=torch.int32, device=dev)
+        wsb_i = cox.cox_integral_image_workspace(B, H, W)
+        ws_i = torch.empty(wsb_i, dtype=torch.uint8, device=dev)
+        ms = _time_launches(st, lambda: chk(cox.cox_integral_image(code, B, H, W, img.data_ptr(), ii.data_ptr(),
+                                                                   ws_i.data_ptr(), wsb_i, sh)))
+        gbs = B * H * W * (bpp + 4) / (ms * 1e-3) / 1e9
+        second[name] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3),
+                        "algorithmic_bytes_per_pixel": bpp + 4}
+        del img, ii, ws_i
+    res["vote_stats_and_integral_image"] = second
+
     res["batched_10000_uneven"] = run_batched(dev, st)
     res["serving"] = run_serving(dev)
 

@@ -54,7 +54,7 @@ typedef enum {
   COX_EBUSY = 6          /* resource in use (server: no free slot) */
 } cox_status;
 
-typedef enum { COX_I32 = 0, COX_U32 = 1, COX_F32 = 2 } cox_dtype;
+typedef enum { COX_I32 = 0, COX_U32 = 1, COX_F32 = 2, COX_U8 = 3 /* cox_integral_image input only */ } cox_dtype;
 
 typedef enum { COX_SUM = 0, COX_MIN = 1, COX_MAX = 2, COX_AND = 3, COX_OR = 4, COX_XOR = 5 } cox_op;
 
@@ -252,6 +252,35 @@ cox_status cox_coalesced(cox_cgfn fn, cox_dtype dt, int block_dim, const void* d
  */
 cox_status cox_filter_aggregated(cox_dtype dt, const void* d_keys, int64_t n, int64_t threshold, void* d_out,
                                  int64_t* d_count, void* stream);
+
+/*
+ * cox_vote_stats -- batched statistics of the SDK's vote kernels (VoteAny /
+ * VoteAll, Table 1): d_pred (n 32-bit values, predicate = value != 0; fp32
+ * 0.0f and -0.0f are false) is cut into segments of seg_len elements (a
+ * multiple of width; the last segment may be shorter) and each segment into
+ * tiles of `width` lanes, whose tile-local ballot gives any/all/popcount.
+ * d_stats (3 int64 per segment, zeroed by the call): [tiles with any() true,
+ * tiles with all() true, true predicates].  A ragged last tile's missing
+ * lanes are padding with a false predicate, so its all() is false.
+ */
+cox_status cox_vote_stats(cox_dtype dt, int width, const void* d_pred, int64_t n, int64_t seg_len, int64_t* d_stats,
+                          void* stream);
+
+/*
+ * cox_integral_image -- integral images of a batch of `batch` images of
+ * height x width pixels, stored contiguously (image b, row y, column x at
+ * (b*height + y)*width + x): out = sum over y' <= y, x' <= x, mod 2^32 --
+ * the SDK's shfl_intimage_rows + shfl_vertical_shfl pair (Table 1).
+ * in_dt: COX_U8 (uint8 pixels) or COX_U32 / COX_I32 (32-bit, summed mod
+ * 2^32).  d_out: batch*height*width uint32.  d_workspace:
+ * cox_integral_image_workspace() bytes (per image row, the prefix of each
+ * 32-pixel strip), 16-byte aligned.  Two kernels: strip prefixes per row,
+ * then one warp per 32-column strip walks the rows (shuffle row scan plus
+ * the strip prefix, running column sums).
+ */
+cox_status cox_integral_image(cox_dtype in_dt, int64_t batch, int64_t height, int64_t width, const void* d_in,
+                              uint32_t* d_out, void* d_workspace, size_t workspace_bytes, void* stream);
+size_t cox_integral_image_workspace(int64_t batch, int64_t height, int64_t width);
 
 /*
  * cox_ballot_compact -- stable stream compaction driven by warp ballots.

@@ -17,7 +17,7 @@ from .build import lib_path
 
 # ------------------------------------------------------------------ codes
 COX_OK, COX_EINVAL, COX_EUNSUPPORTED, COX_ECUDA, COX_ENOMEM, COX_ETIMEOUT, COX_EBUSY = range(7)
-COX_I32, COX_U32, COX_F32 = 0, 1, 2
+COX_I32, COX_U32, COX_F32, COX_U8 = 0, 1, 2, 3
 COX_SUM, COX_MIN, COX_MAX, COX_AND, COX_OR, COX_XOR = range(6)
 (COX_SHFL_IDX, COX_SHFL_UP, COX_SHFL_DOWN, COX_SHFL_XOR,
  COX_BALLOT, COX_ANY, COX_ALL, COX_MATCH_ANY) = range(8)
@@ -48,6 +48,9 @@ SIGNATURES = {
     "cox_grid_broadcast_workspace": (_SZ, [_I64]),
     "cox_coalesced": (_I, [_I, _I, _I, _P, _P, _P, _I64, _I, _P]),
     "cox_filter_aggregated": (_I, [_I, _P, _I64, _I64, _P, _P, _P]),
+    "cox_vote_stats": (_I, [_I, _I, _P, _I64, _I64, _P, _P]),
+    "cox_integral_image": (_I, [_I, _I64, _I64, _I64, _P, _P, _P, _SZ, _P]),
+    "cox_integral_image_workspace": (_SZ, [_I64, _I64, _I64]),
     "cox_ballot_compact": (_I, [_I, _I, _I, _P, _I64, _I64, _P, _P, _P, _SZ, _U, _P]),
     "cox_ballot_compact_workspace": (_SZ, [_I64, _I]),
     "cox_ballot_compact_static": (_I, [_I, _I, _I, _P, _I64, _I64, _P, _P, _P]),
@@ -148,6 +151,18 @@ def cox_coalesced(fn, dt, block_dim, d_in, d_active, d_out, n, param, stream) ->
 
 def cox_filter_aggregated(dt, d_keys, n, threshold, d_out, d_count, stream) -> int:
     return lib().cox_filter_aggregated(dt, d_keys, n, threshold, d_out, d_count, stream)
+
+
+def cox_vote_stats(dt, width, d_pred, n, seg_len, d_stats, stream) -> int:
+    return lib().cox_vote_stats(dt, width, d_pred, n, seg_len, d_stats, stream)
+
+
+def cox_integral_image(in_dt, batch, height, width, d_in, d_out, d_ws, ws_bytes, stream) -> int:
+    return lib().cox_integral_image(in_dt, batch, height, width, d_in, d_out, d_ws, ws_bytes, stream)
+
+
+def cox_integral_image_workspace(batch, height, width) -> int:
+    return lib().cox_integral_image_workspace(batch, height, width)
 
 
 def cox_ballot_compact(dt, width, block_dim, d_keys, n, threshold, d_out, d_count, d_ws, ws_bytes, flags,
