@@ -32,7 +32,8 @@ def dev(a):
 @pytest.mark.parametrize("density", [0.0, 0.05, 0.5, 0.97, 1.0])
 def test_vote_stats(cox, W, density):
     import torch
-    for n, seg in ((1, 32), (1000, 64), (70_001, 1024), (70_001, 4096 + 32), (1 << 20, 16384), (5000, W)):
+    for n, seg in ((1, 32), (1000, 64), (70_001, 1024), (70_001, 4096 + 32), (1 << 20, 16384), (5000, W),
+                   (70_001, 4096), ((1 << 20) + 77, 8192)):  # 16384, 4096, 8192: the 128-bit-load kernel
         thr = inputs.density_threshold(density) if density < 1 else 2**31
         pred = (inputs.uniform_u31(n, seed=n + W) < thr).astype(np.int32) * \
             (1 + (inputs.bits_u32(n, seed=n) & 7).astype(np.int32))
