@@ -136,6 +136,79 @@ __device__ typename R::V look_back_op(uint32_t* flags, uint64_t* agg, uint64_t* 
   return prefix;
 }
 
+// Look-back for 32-bit scan values over packed descriptors: desc[t] =
+// (state << 32) | value bits, state 0 nothing, 1 aggregate, 2 inclusive
+// prefix, so one relaxed 64-bit load returns a consistent (state, value)
+// pair (one round trip per window, no second load).  Same walk as
+// look_back_op.  Returns the tile's exclusive prefix.
+template <class R>
+__device__ typename R::V look_back_packed(uint64_t* desc, int64_t tile, typename R::V total, uint32_t limit,
+                                          unsigned* status, bool& gave_up) {
+  using V = typename R::V;
+  using T = typename R::T;
+  const int lane = lane_id();
+  gave_up = false;
+  if (tile == 0) {
+    if (lane == 0) st_relaxed_u64(desc, (2ull << 32) | to_bits(total));
+    return R::ident();
+  }
+  if (lane == 0) st_relaxed_u64(desc + tile, (1ull << 32) | to_bits(total));
+  V prefix = R::ident();
+  uint32_t polls = 0;
+  bool timed_out = false;
+  for (int64_t w0 = tile - 1;; w0 -= 32 * kScanLookV) {
+    uint64_t d[kScanLookV];
+#pragma unroll
+    for (int v = 0; v < kScanLookV; ++v) {
+      const int64_t i = w0 - (lane * kScanLookV + v);
+      d[v] = i >= 0 ? ld_relaxed_u64(desc + i) : ((2ull << 32) | to_bits(R::ident()));  // before tile 0
+    }
+    int lp;
+    unsigned pm;
+    for (;;) {
+      lp = kScanLookV;
+#pragma unroll
+      for (int v = kScanLookV - 1; v >= 0; --v)
+        if ((d[v] >> 32) == 2u) lp = v;
+      pm = __ballot_sync(kFull, lp < kScanLookV);
+      const int fl = pm ? __ffs(pm) - 1 : 32;
+      bool missing = false;
+#pragma unroll
+      for (int v = 0; v < kScanLookV; ++v)
+        if ((lane < fl || (lane == fl && v <= lp)) && (d[v] >> 32) == 0u) missing = true;
+      if (!__any_sync(kFull, missing)) break;
+      if (++polls > limit) {
+        timed_out = true;
+        break;
+      }
+      if (polls > 64) __nanosleep(64);
+#pragma unroll
+      for (int v = 0; v < kScanLookV; ++v) {
+        const int64_t i = w0 - (lane * kScanLookV + v);
+        if ((d[v] >> 32) == 0u && i >= 0) d[v] = ld_relaxed_u64(desc + i);
+      }
+    }
+    if (timed_out) break;
+    const int fl = pm ? __ffs(pm) - 1 : 32;
+    V part = R::ident();
+#pragma unroll
+    for (int v = kScanLookV - 1; v >= 0; --v)  // older tiles first
+      if (lane < fl || (lane == fl && v <= lp)) part = R::op(from_bits<T>((uint32_t)d[v]), part);
+    prefix = R::op(warp_fold<R>(part), prefix);
+    if (pm) break;
+  }
+  if (__any_sync(kFull, timed_out)) {
+    gave_up = true;
+    if (lane == 0) {
+      atomicOr(status, (unsigned)kDevTimeout);
+      st_relaxed_u64(desc + tile, (2ull << 32) | to_bits(total));  // release successors
+    }
+    return R::ident();
+  }
+  if (lane == 0) st_relaxed_u64(desc + tile, (2ull << 32) | to_bits(R::op(prefix, total)));
+  return prefix;
+}
+
 template <class R>
 __host__ __device__ constexpr int grid_scan_tile() {
   return R::kComp ? 8192 : 16384;
@@ -265,6 +338,182 @@ __global__ void __launch_bounds__(256) k_scan_grid(const uint32_t* __restrict__ 
   }
 }
 
+// GRID scope over aligned arrays of at least one full row: tiles of 512 rows
+// of 32 elements (16384) arrive by two 2D TMA boxes with 128-byte swizzle;
+// lane t of warp w owns rows 64w + t and 64w + 32 + t of the tile.  Pass A
+// folds each row (its total), shuffle scans over the warp's 64 rows and a
+// scan of the 8 warp totals give every row's exclusive prefix, the tile
+// looks back for its own prefix (32-bit values: packed state|value
+// descriptors in `agg`), and pass B re-reads the row, carrying
+// prefix op value into each element (in place), before one TMA store.
+// Sums are folded left to right within a row, so fp32 results differ from
+// the shuffle form in their last bits (tolerance-checked).  The partial last
+// row (n % 32 elements) is read and written by its lane from global memory.
+constexpr int kGridRowsTile = 512;  // rows per tile: two TMA boxes of 256 rows
+constexpr int kGridBoxRows = 256;
+
+template <class R>
+__global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ CUtensorMap tin,
+                                                        const __grid_constant__ CUtensorMap tout,
+                                                        const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                        int64_t n, unsigned* ticket, uint32_t* flags, uint64_t* agg,
+                                                        uint64_t* inc, int64_t ntiles, int excl, uint32_t limit,
+                                                        unsigned* status) {
+  using T = typename R::T;
+  using V = typename R::V;
+  extern __shared__ uint8_t gsr_raw[];
+  uint4* buf = reinterpret_cast<uint4*>((reinterpret_cast<uintptr_t>(gsr_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t s_bar;
+  __shared__ V s_wtot[8], s_cp[8];
+  __shared__ int64_t s_tile;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t rows = n / 32;
+  if (tid == 0) {
+    s_tile = atomicAdd(ticket, 1u);
+    s_bad = 0;
+    mbar_init(&s_bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const int64_t tile = s_tile;
+  if (tile >= ntiles) return;
+  const int64_t r0 = tile * kGridRowsTile;
+  const int nbox = r0 >= rows ? 0 : (r0 + kGridBoxRows >= rows ? 1 : 2);  // boxes holding full rows
+  if (tid == 0 && nbox > 0) {
+    mbar_arrive_expect_tx(&s_bar, (uint32_t)nbox * kGridBoxRows * 128u);
+    for (int bx = 0; bx < nbox; ++bx)
+      tma_load_2d(buf + bx * kGridBoxRows * 8, &tin, 0, (int)(r0 + bx * kGridBoxRows), &s_bar);
+  }
+  // lane owns rows rl0 = 64w + lane and rl1 = rl0 + 32 of the tile
+  const int rl0 = warp * 64 + lane, rl1 = rl0 + 32;
+  const uint32_t pad = to_bits(R::pad());
+  if (nbox > 0) {
+    const bool ok = mbar_wait_bounded(&s_bar, 0u, limit);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(status, (unsigned)kDevTimeout);
+        mbar_wait_bounded(&s_bar, 0u, limit);
+        if constexpr (R::kComp) {
+          st_relaxed_u64(inc + tile, pack<R>(R::ident()));
+          st_release_u32(flags + tile, 2u);
+        } else {
+          st_relaxed_u64(agg + tile, (2ull << 32) | to_bits(R::ident()));
+        }
+      }
+      return;
+    }
+  }
+  // The partial last row (n % 32 elements) comes from global memory, after the
+  // boxes have landed (they fill rows past the end with zeros).
+  auto fill_partial = [&](int rl) {
+    const int64_t row = r0 + rl;
+    if (!(row == rows && rows * 32 < n)) return;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t e = row * 32 + 4 * j;
+      uint4 q;
+      q.x = e < n ? in[e] : pad;
+      q.y = e + 1 < n ? in[e + 1] : pad;
+      q.z = e + 2 < n ? in[e + 2] : pad;
+      q.w = e + 3 < n ? in[e + 3] : pad;
+      buf[rl * 8 + (j ^ (rl & 7))] = q;
+    }
+  };
+  fill_partial(rl0);
+  fill_partial(rl1);
+  // ---- pass A: row totals (left folds)
+  auto row_total = [&](int rl) {
+    V tot = R::ident();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint4 q = buf[rl * 8 + (j ^ (rl & 7))];
+      tot = R::op(tot, R::load(from_bits<T>(q.x)));
+      tot = R::op(tot, R::load(from_bits<T>(q.y)));
+      tot = R::op(tot, R::load(from_bits<T>(q.z)));
+      tot = R::op(tot, R::load(from_bits<T>(q.w)));
+    }
+    return tot;
+  };
+  auto warp_incl = [&](V v) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const V u = R::shfl_up(v, d, 32);
+      if (lane >= d) v = R::op(u, v);
+    }
+    return v;
+  };
+  const V i0 = warp_incl(row_total(rl0));
+  const V t0 = R::shfl_idx(i0, 31, 32);
+  const V i1 = R::op(t0, warp_incl(row_total(rl1)));
+  const V e0 = R::shfl_up(i0, 1, 32), e1 = R::shfl_up(i1, 1, 32);
+  const V pre0 = lane == 0 ? R::ident() : e0;
+  const V pre1 = lane == 0 ? t0 : e1;
+  if (lane == 31) s_wtot[warp] = i1;
+  __syncthreads();
+  if (warp == 0) {
+    V total = R::ident();
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        s_cp[k] = total;
+        total = R::op(total, s_wtot[k]);
+      }
+    }
+    total = R::shfl_idx(total, 0, 32);
+    bool gave_up;
+    V prefix;
+    if constexpr (R::kComp) prefix = look_back_op<R>(flags, agg, inc, tile, total, limit, status, gave_up);
+    else prefix = look_back_packed<R>(agg, tile, total, limit, status, gave_up);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s_cp[k] = R::op(prefix, s_cp[k]);
+      s_bad = gave_up;
+    }
+  }
+  __syncthreads();
+  if (s_bad) return;
+  // ---- pass B: carry prefix op value through each row, in place
+  auto carry_row = [&](int rl, V carry) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      uint4& slot = buf[rl * 8 + (j ^ (rl & 7))];
+      uint4 q = slot;
+      uint32_t* w = &q.x;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const V nx = R::op(carry, R::load(from_bits<T>(w[k])));
+        w[k] = to_bits(R::out(excl ? carry : nx));
+        carry = nx;
+      }
+      slot = q;
+    }
+  };
+  const V cw = s_cp[warp];
+  carry_row(rl0, R::op(cw, pre0));
+  carry_row(rl1, R::op(cw, pre1));
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (tid == 0)
+    for (int bx = 0; bx < nbox; ++bx) tma_store_2d(&tout, 0, (int)(r0 + bx * kGridBoxRows), buf + bx * kGridBoxRows * 8);
+  auto store_partial = [&](int rl) {
+    const int64_t row = r0 + rl;
+    if (!(row == rows && rows * 32 < n)) return;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint4 q = buf[rl * 8 + (j ^ (rl & 7))];
+      const int64_t e = row * 32 + 4 * j;
+      if (e < n) out[e] = q.x;
+      if (e + 1 < n) out[e + 1] = q.y;
+      if (e + 2 < n) out[e + 2] = q.z;
+      if (e + 3 < n) out[e + 3] = q.w;
+    }
+  };
+  store_partial(rl0);
+  store_partial(rl1);
+  if (tid == 0 && nbox > 0) tma_store_wait_read();  // the boxes have left shared memory
+}
+
 // BLOCK scope: the CTA is the logical block (persistent over blocks).
 template <class R>
 __global__ void __launch_bounds__(1024) k_scan_block(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
@@ -347,6 +596,28 @@ static cox_status launch_scan_scope(cox_scope scope, int block, const void* d_in
     if (g == 0) g = persistent_grid(k, block, 0, 1 << 30);
     const int64_t nblk = (n + block - 1) / block;
     k<<<(int)(nblk < g ? nblk : g), block, 0, st>>>(in, out, n, excl);
+    return launch_status();
+  }
+  if (n >= 32 && n / 32 < (int64_t(1) << 31) && aligned16(d_in) && aligned16(d_out)) {
+    const int64_t ntiles = (n + kGridRowsTile * 32 - 1) / (kGridRowsTile * 32);
+    const size_t need = scan_ws_bytes(ntiles);
+    if (!ws || ws_bytes < need) return COX_ENOMEM;
+    if (!aligned16(ws)) return COX_EINVAL;
+    CUtensorMap tin, tout;
+    if (!encode_rows32_map(&tin, d_in, n / 32, kGridBoxRows) || !encode_rows32_map(&tout, d_out, n / 32, kGridBoxRows))
+      return COX_ECUDA;
+    if (cudaMemsetAsync(ws, 0, need, st) != cudaSuccess) return COX_ECUDA;
+    const ScanWs w = scan_ws(ws, ntiles);
+    auto k = k_scan_grid_rows<R>;
+    const size_t smem = (size_t)kGridRowsTile * 128 + 1024;
+    static bool attr = false;
+    if (!attr) {
+      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return COX_ECUDA;
+      attr = true;
+    }
+    k<<<(unsigned)ntiles, 256, smem, st>>>(tin, tout, in, out, n, w.ticket, w.flags, w.agg, w.inc, ntiles, excl,
+                                           spin_limit(), device_status_word());
     return launch_status();
   }
   constexpr int TILE = grid_scan_tile<R>();
