@@ -273,10 +273,11 @@ cox_status cox_vote_stats(cox_dtype dt, int width, const void* d_pred, int64_t n
  * the SDK's shfl_intimage_rows + shfl_vertical_shfl pair (Table 1).
  * in_dt: COX_U8 (uint8 pixels) or COX_U32 / COX_I32 (32-bit, summed mod
  * 2^32).  d_out: batch*height*width uint32.  d_workspace:
- * cox_integral_image_workspace() bytes (per image row, the prefix of each
- * 32-pixel strip), 16-byte aligned.  Two kernels: strip prefixes per row,
- * then one warp per 32-column strip walks the rows (shuffle row scan plus
- * the strip prefix, running column sums).
+ * cox_integral_image_workspace() bytes (per image row the prefix of each
+ * 32-pixel strip; per image, band of 64 rows and column a band prefix),
+ * 16-byte aligned.  Strip prefixes per row, band column sums and their
+ * prefixes, then one warp per (image, band, 32-column strip) walks the
+ * band's rows (shuffle row scan plus the strip prefix, running column sums).
  */
 cox_status cox_integral_image(cox_dtype in_dt, int64_t batch, int64_t height, int64_t width, const void* d_in,
                               uint32_t* d_out, void* d_workspace, size_t workspace_bytes, void* stream);
