@@ -44,11 +44,12 @@ WORKLOAD = ("tile inclusive scan (shfl_up, cg tiles) of 2^26 fp32 N(0,1) at widt
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture, valid
 # only while the kernel sources hash to `src_sha` (else reported as null).
-NCU_TRAFFIC = {"src_sha": "6c43a17ef0f4328a",  # profiles/tile_scan_2p26_fp32_ncu.md
-               "bytes_per_launch": {"k_tile_scan_rows<Comp, 32>": 268489728 + 217500416,
-                                    "k_tile_scan_rows<Comp, 16>": 268482560 + 216888832,
-                                    "k_tile_scan_rows<Plain<AddF>, 32>": 268497152 + 216726528,
-                                    "k_tile_scan_rows<Plain<AddF>, 16>": 268458496 + 217366784}}
+NCU_TRAFFIC = {"src_sha": "4b92ae71bd58becc",  # profiles/tile_scan_2p26_fp32_ncu.md
+               "bytes_per_launch": {
+                                    "k_tile_scan_rows<Plain<AddF>, 16>": 268465152 + 216230400,
+                                    "k_tile_scan_rows<Comp, 16>": 268500480 + 217132800,
+                                    "k_tile_scan_rows<Plain<AddF>, 32>": 268462336 + 216157440,
+                                    "k_tile_scan_rows<Comp, 32>": 268521984 + 218140672}}
 KERNEL_SOURCES = ["paper_2112_10034_gb300/csrc/scan.cu", "paper_2112_10034_gb300/csrc/cox_common.cuh"]
 
 
@@ -761,7 +762,9 @@ def run_profile(args):
     one 2^26-element input and one output; `compact` runs 2^26-key compactions
     at density 0.5; `hist` runs 2^26-key Zipf match histograms; `batch` runs
     the batched kernel on 1000 arrays of the batched length law (~1e8
-    elements)."""
+    elements); `gridscan` a 2^26 int32 grid-scope scan; `reduce` a 2^26 fp32
+    compensated tile reduce (W 32) then block reduce (B 256); `intimage` the
+    integral images of 64 8-bit 1080x1920 frames (three kernels)."""
     import torch
     from paper_2112_10034_gb300 import cox
     dev = torch.device("cuda", 0)
@@ -791,6 +794,32 @@ def run_profile(args):
             chk(cox.cox_ballot_compact(0, 32, 256, k.data_ptr(), N_ELEMS, inputs.density_threshold(0.5),
                                        out.data_ptr(), cnt.data_ptr(), ws.data_ptr(), wsb, 0, sh))
         launches = reps
+    elif args.profile == "gridscan":
+        xi = torch.randint(-1000, 1001, (N_ELEMS,), device=dev, dtype=torch.int32)
+        yi = torch.empty_like(xi)
+        wsb = cox.cox_scan_workspace(2, N_ELEMS)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        for _ in range(reps):
+            chk(cox.cox_scan(0, 0, 2, 256, xi.data_ptr(), yi.data_ptr(), N_ELEMS, 0, 0, ws.data_ptr(), wsb, sh))
+        launches = reps
+    elif args.profile == "reduce":
+        x = torch.from_numpy(inputs.normal_f32(N_ELEMS, inputs.BASE_SEED + 1)).to(dev)
+        y = torch.empty(N_ELEMS // 32, dtype=torch.float32, device=dev)
+        ylo = torch.empty(N_ELEMS // 32, dtype=torch.float32, device=dev)
+        for _ in range(reps):  # tile reduce W=32 compensated with low words, then block reduce B=256
+            chk(cox.cox_tile_reduce(0, 2, 32, 256, 0, x.data_ptr(), y.data_ptr(), N_ELEMS, 1, ylo.data_ptr(), None, 0,
+                                    sh))
+            chk(cox.cox_tile_reduce(0, 2, 32, 256, 1, x.data_ptr(), y.data_ptr(), N_ELEMS, 1, None, None, 0, sh))
+        launches = reps * 2
+    elif args.profile == "intimage":
+        B, H, W = 64, 1080, 1920
+        img = torch.randint(0, 256, (B * H * W // 4,), device=dev, dtype=torch.int32)
+        ii = torch.empty(B * H * W, dtype=torch.int32, device=dev)
+        wsb = cox.cox_integral_image_workspace(B, H, W)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        for _ in range(reps):
+            chk(cox.cox_integral_image(3, B, H, W, img.data_ptr(), ii.data_ptr(), ws.data_ptr(), wsb, sh))
+        launches = reps * 3
     elif args.profile == "batch":
         lens = inputs.loguniform_lengths(1000, 32, 1 << 20, inputs.BASE_SEED + 3)
         vals = [torch.randn(int(L), device=dev) for L in lens]
@@ -818,7 +847,8 @@ def main():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--profile", choices=["scan", "compact", "hist", "batch"], default=None,
+    ap.add_argument("--profile", choices=["scan", "compact", "hist", "batch", "gridscan", "reduce", "intimage"],
+                    default=None,
                     help="small single-op case for ncu captures")
     args = ap.parse_args()
     if args.warmup < 3:
