@@ -323,9 +323,10 @@ size_t cox_ballot_compact_workspace(int64_t n, int block_dim);
  * Same arguments and results as cox_ballot_compact minus the workspace and
  * flags.  The scratch is a fixed array of COX_COMPACT_STATIC_SCRATCH_BYTES
  * (1 MiB) inside libcox.so, held on every GPU that loads the library until
- * the process exits.  It fits 256 bytes of header plus 8 bytes per tile of
- * 16384 keys: n <= 131040 * 16384 (2,146,959,360 keys).  Larger n returns
- * COX_ENOMEM before anything is enqueued.
+ * the process exits.  It fits 256 bytes of header, 8 bytes per tile of
+ * 16384 keys and 16 bytes per group of 32 tiles: n <= 123330 * 16384
+ * (2,020,638,720 keys).  Larger n returns COX_ENOMEM before anything is
+ * enqueued.
  * The call allocates nothing (no cudaMalloc/cudaFree) and clears the scratch
  * bytes it uses with a cudaMemsetAsync on `stream` before its kernel.
  * The first call on a device looks up the array's device address (with that

@@ -85,8 +85,7 @@ using namespace cox;
 extern "C" size_t cox_ballot_compact_workspace(int64_t n, int block_dim) {
   if (n < 0 || !valid_block(block_dim)) return 0;
   const int64_t tile = kBigTile;
-  const int64_t ntiles = (n + tile - 1) / tile;
-  return kCompactWsHeader + (size_t)ntiles * sizeof(uint64_t);
+  return compact_ws_bytes((n + tile - 1) / tile);
 }
 
 extern "C" cox_status cox_ballot_compact(cox_dtype dt, int width, int block_dim, const void* d_keys, int64_t n,

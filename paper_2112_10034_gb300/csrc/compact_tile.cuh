@@ -9,6 +9,8 @@
 // a single-pass decoupled look-back over per-tile descriptors.  A tile only
 // waits on tiles with smaller indexes, which callers hand out in order to
 // CTAs that already run, so the waits end; each wait is still bounded.
+// The look-back has two levels: within a group of 32 tiles, then over whole
+// groups (their counts summed by atomics as the last tile of each arrives).
 //
 // Tile layout: a tile of kBigTile = 16384 keys sits in shared memory.  Warp
 // w of pass j owns the run of 512 keys at 16Bj + 512w; its lanes read them
@@ -28,78 +30,128 @@ constexpr uint64_t kFlagA = 1ull << 62;  // descriptor holds the tile's own coun
 constexpr uint64_t kFlagP = 2ull << 62;  // descriptor holds the inclusive prefix
 constexpr uint64_t kValMask = (1ull << 62) - 1;
 
-// Look-back by one warp, after the tile published its own count (flag A; P
-// for tile 0).  The warp reads a window of 32 * kLookV predecessors at a
-// time -- lane l holds positions l*kLookV .. l*kLookV + kLookV - 1 counted
-// back from the tile -- and stops at the closest published inclusive prefix
-// (flag P), adding the counts of the tiles in between.  Only descriptors
-// closer than that prefix must be published; the warp re-polls just those,
-// tightly at first and then with a short back-off, for at most `limit`
-// rounds.  Returns the tile's exclusive prefix (every lane) and publishes the
-// tile's inclusive prefix.  On time-out: records kDevTimeout, publishes a zero
-// prefix so successors end, and sets gave_up.
-constexpr int kLookV = 4;
+// Two-level decoupled look-back over tile counts.  Tiles form groups of 32
+// (group g = tiles 32g .. 32g+31).  Next to the per-tile descriptors
+// desc[0 .. ntiles) the workspace holds, per group, a descriptor gdesc[g]
+// and an accumulator gacc[g] = (arrivals << 48) | running count.  A tile
+// publishes its count (flag A; tile 0: flag P) and adds (1 << 48) | count to
+// its group's accumulator; the add that completes a group publishes the
+// group's count (flag A) in gdesc[g].  A tile publishes its inclusive prefix
+// (flag P) when its look-back ends, and the group's last tile also puts it
+// in gdesc[g] (atomicMax: a P word is larger than any A word, so a late A
+// never hides a P).  The look-back first reads the tile's own group
+// (positions below it): the closest P there, plus the counts after it, is
+// the answer; otherwise the in-group counts are summed and the warp walks
+// back over whole groups, 32 groups (1024 tiles) per window, to the closest
+// group with P, adding the counts of the groups in between.  A tile that
+// runs ahead only ever waits on tiles with smaller indexes.  Every wait is
+// bounded by `limit` polls; on time-out the tile records kDevTimeout and
+// publishes a zero prefix so its successors end.
+constexpr int kGroupShift = 5;  // 32 tiles per group
+constexpr uint64_t kGroupArrive = 1ull << 48;
+constexpr uint64_t kGroupSumMask = kGroupArrive - 1;
 
-__device__ __forceinline__ int64_t look_back(uint64_t* desc, int64_t tile, uint32_t total, uint32_t limit,
-                                             unsigned* status, bool& gave_up) {
+__host__ __device__ inline int64_t compact_groups(int64_t ntiles) {
+  return (ntiles + (1 << kGroupShift) - 1) >> kGroupShift;
+}
+// Workspace bytes of a compaction over ntiles tiles: header (ticket), tile
+// descriptors, group descriptors and group accumulators.
+__host__ __device__ inline size_t compact_ws_bytes(int64_t ntiles) {
+  return kCompactWsHeader + (size_t)ntiles * 8 + (size_t)compact_groups(ntiles) * 16;
+}
+
+// Publishes a tile's own count (lane 0 of the looking-back warp).
+__device__ __forceinline__ void publish_count(uint64_t* desc, int64_t tile, int64_t ntiles, uint32_t total) {
+  st_relaxed_u64(desc + tile, (tile == 0 ? kFlagP : kFlagA) | total);
+  uint64_t* gdesc = desc + ntiles;
+  uint64_t* gacc = gdesc + compact_groups(ntiles);
+  const int64_t g = tile >> kGroupShift;
+  const int64_t gsize = min((int64_t)1 << kGroupShift, ntiles - (g << kGroupShift));
+  const unsigned long long old = atomicAdd(reinterpret_cast<unsigned long long*>(gacc + g), kGroupArrive | total);
+  if ((int64_t)(old >> 48) + 1 == gsize)
+    atomicMax(reinterpret_cast<unsigned long long*>(gdesc + g), kFlagA | ((old + total) & kGroupSumMask));
+}
+
+// The tile's exclusive prefix (every lane of the calling warp); lane 0
+// publishes the inclusive prefix.
+__device__ __forceinline__ int64_t look_back(uint64_t* desc, int64_t tile, int64_t ntiles, uint32_t total,
+                                             uint32_t limit, unsigned* status, bool& gave_up) {
   const int lane = lane_id();
   gave_up = false;
-  if (tile == 0) return 0;
+  uint64_t* gdesc = desc + ntiles;
+  const int64_t g = tile >> kGroupShift;
+  const int pos = (int)(tile & ((1 << kGroupShift) - 1));
   int64_t prefix = 0;
   uint32_t polls = 0;
   bool timed_out = false;
-  for (int64_t w0 = tile - 1;; w0 -= 32 * kLookV) {
-    uint64_t d[kLookV];
-#pragma unroll
-    for (int v = 0; v < kLookV; ++v) {
-      const int64_t i = w0 - (lane * kLookV + v);
-      d[v] = i >= 0 ? ld_relaxed_u64(desc + i) : kFlagP;  // before tile 0: prefix 0
-    }
-    int lp;
+  bool done = tile == 0;
+  // ---- the tile's own group: lane l holds position l < pos
+  if (!done && pos > 0) {
+    const int64_t g0 = g << kGroupShift;
+    uint64_t d = lane < pos ? ld_relaxed_u64(desc + g0 + lane) : kFlagA;
     unsigned pm;
+    int fl;
     for (;;) {
-      lp = kLookV;
-#pragma unroll
-      for (int v = kLookV - 1; v >= 0; --v)
-        if ((d[v] >> 62) == 2) lp = v;
-      pm = __ballot_sync(kFull, lp < kLookV);
-      const int fl = pm ? __ffs(pm) - 1 : 32;  // lane holding the closest prefix
-      bool missing = false;
-#pragma unroll
-      for (int v = 0; v < kLookV; ++v)
-        if ((lane < fl || (lane == fl && v <= lp)) && (d[v] >> 62) == 0) missing = true;
+      pm = __ballot_sync(kFull, lane < pos && (d >> 62) == 2);
+      fl = pm ? 31 - __clz(pm) : -1;  // closest inclusive prefix: the highest position
+      const bool missing = lane < pos && lane > fl && (d >> 62) == 0;
       if (!__any_sync(kFull, missing)) break;
       if (++polls > limit) {
         timed_out = true;
         break;
       }
-      if (polls > 64) __nanosleep(100);
-#pragma unroll
-      for (int v = 0; v < kLookV; ++v) {
-        const int64_t i = w0 - (lane * kLookV + v);
-        if ((d[v] >> 62) == 0 && i >= 0) d[v] = ld_relaxed_u64(desc + i);
-      }
+      if (polls > 64) __nanosleep(64);
+      if (missing) d = ld_relaxed_u64(desc + g0 + lane);
     }
-    if (timed_out) break;
-    const int fl = pm ? __ffs(pm) - 1 : 32;
-    unsigned long long sum = 0;
+    if (!__any_sync(kFull, timed_out)) {
+      unsigned long long v = (lane < pos && lane >= fl) ? (d & kValMask) : 0ull;
 #pragma unroll
-    for (int v = 0; v < kLookV; ++v)
-      if (lane < fl || (lane == fl && v <= lp)) sum += d[v] & kValMask;
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+      prefix = (int64_t)v;
+      done = fl >= 0;
+    }
+  }
+  // ---- whole groups before it: lane l holds group gw - l
+  if (!done && !__any_sync(kFull, timed_out)) {
+    for (int64_t gw = g - 1;; gw -= 32) {
+      const int64_t gi = gw - lane;
+      uint64_t d = gi >= 0 ? ld_relaxed_u64(gdesc + gi) : kFlagP;  // before group 0: prefix 0
+      unsigned pm;
+      for (;;) {
+        pm = __ballot_sync(kFull, (d >> 62) == 2);
+        const int fl = pm ? __ffs(pm) - 1 : 32;  // closest group with an inclusive prefix
+        const bool missing = lane <= fl && (d >> 62) == 0;
+        if (!__any_sync(kFull, missing)) break;
+        if (++polls > limit) {
+          timed_out = true;
+          break;
+        }
+        if (polls > 64) __nanosleep(64);
+        if (missing && gi >= 0) d = ld_relaxed_u64(gdesc + gi);
+      }
+      if (__any_sync(kFull, timed_out)) break;
+      const int fl = pm ? __ffs(pm) - 1 : 32;
+      unsigned long long v = lane <= fl ? (d & kValMask) : 0ull;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFull, sum, off);
-    prefix += (int64_t)sum;
-    if (pm) break;
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+      prefix += (int64_t)v;
+      if (pm) break;
+    }
   }
   if (__any_sync(kFull, timed_out)) {
     gave_up = true;
     if (lane == 0) {
       atomicOr(status, (unsigned)kDevTimeout);
       st_relaxed_u64(desc + tile, kFlagP);  // release successors with a zero prefix
+      if (pos == (1 << kGroupShift) - 1) atomicMax(reinterpret_cast<unsigned long long*>(gdesc + g), kFlagP);
     }
     return 0;
   }
-  if (lane == 0) st_relaxed_u64(desc + tile, kFlagP | ((uint64_t)(prefix + total) & kValMask));
+  if (lane == 0) {
+    const uint64_t inc = kFlagP | ((uint64_t)(prefix + total) & kValMask);
+    if (tile != 0) st_relaxed_u64(desc + tile, inc);
+    if (pos == (1 << kGroupShift) - 1) atomicMax(reinterpret_cast<unsigned long long*>(gdesc + g), inc);
+  }
   return prefix;
 }
 
@@ -246,7 +298,7 @@ __device__ __forceinline__ void compact_big_tile(uint32_t* buf, int valid, int64
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     if (lane == 0) {
-      st_relaxed_u64(desc + tile, (tile == 0 ? kFlagP : kFlagA) | total);
+      publish_count(desc, tile, ntiles, total);
       s_total = total;
     }
   }
@@ -261,7 +313,7 @@ __device__ __forceinline__ void compact_big_tile(uint32_t* buf, int valid, int64
   // ---- prefix and copy-out
   if (warp == 0) {
     bool gave_up;
-    const int64_t prefix = look_back(desc, tile, s_total, limit, status, gave_up);
+    const int64_t prefix = look_back(desc, tile, ntiles, s_total, limit, status, gave_up);
     if (lane == 0) {
       s_prefix = prefix;
       s_bad = gave_up;

@@ -276,7 +276,7 @@ __global__ void k_serve_prep(const uint8_t* __restrict__ table) {
   if ((int)blockIdx.x >= hdr->nreq) return;
   const ReqDesc d = reqs[blockIdx.x];
   if (d.kind != COX_REQ_COMPACT) return;
-  const size_t words = (kAlign + (size_t)d.nitems * 8) / 4;
+  const size_t words = compact_ws_bytes(d.nitems) / 4;  // count, tile and group descriptors
   uint32_t* w = reinterpret_cast<uint32_t*>(d.ws);
   for (size_t i = threadIdx.x; i < words; i += blockDim.x) w[i] = 0u;
 }
@@ -295,7 +295,7 @@ void request_bytes(const cox_request& r, size_t* out_b, size_t* ws_b) {
   switch (r.kind) {
     case COX_REQ_REDUCE: *out_b = kAlign; *ws_b = round_up((size_t)items * 8); break;
     case COX_REQ_SCAN: *out_b = round_up((size_t)r.n * 4); *ws_b = 0; break;
-    default: *out_b = round_up((size_t)r.n * 4); *ws_b = kAlign + round_up((size_t)items * 8); break;
+    default: *out_b = round_up((size_t)r.n * 4); *ws_b = round_up(compact_ws_bytes(items)); break;
   }
 }
 

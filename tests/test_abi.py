@@ -53,9 +53,11 @@ def test_workspace_sizes(cox):
     assert cox.cox_tile_reduce_workspace(cox.COX_SCOPE_TILE, 10**6, 256) == 0
     assert cox.cox_tile_reduce_workspace(cox.COX_SCOPE_GRID, 10**6, 256) > 0
     tile = 16384
-    assert cox.cox_ballot_compact_workspace(2**28, 256) == 256 + 8 * (2**28 // tile)
-    assert cox.cox_ballot_compact_workspace(2**28, 1024) == 256 + 8 * (2**28 // tile)
-    assert cox.cox_ballot_compact_workspace(1, 256) == 256 + 8
+    # header + a descriptor per tile + a descriptor and an accumulator per group of 32 tiles
+    t = 2**28 // tile
+    assert cox.cox_ballot_compact_workspace(2**28, 256) == 256 + 8 * t + 16 * ((t + 31) // 32)
+    assert cox.cox_ballot_compact_workspace(2**28, 1024) == 256 + 8 * t + 16 * ((t + 31) // 32)
+    assert cox.cox_ballot_compact_workspace(1, 256) == 256 + 8 + 16
 
 
 @pytest.mark.parametrize("width", [0, 1, 3, 64])
