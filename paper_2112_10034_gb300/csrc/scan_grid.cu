@@ -16,6 +16,8 @@
 // and its inclusive prefix in separate slots, each written before its flag
 // (release store) and read after it (acquire load), so a reader never sees a
 // value from the wrong stage.
+#include <type_traits>
+
 #include "cox_common.cuh"
 
 namespace cox {
@@ -209,6 +211,94 @@ __device__ typename R::V look_back_packed(uint64_t* desc, int64_t tile, typename
   return prefix;
 }
 
+// Two-level form of look_back_packed for 32-bit sums (wrapping adds): tiles
+// form groups of 32; a tile adds (1 << 48) | value to its group's
+// accumulator gacc[g] after publishing its aggregate, and the add that
+// completes the group publishes the group aggregate in gdesc[g]; the last
+// tile of a group also puts its inclusive prefix there (atomicMax: a
+// state-2 word is larger than any state-1 word).  The look-back reads the
+// tile's own group first, then whole groups, 32 per window (1024 tiles), so
+// its length no longer grows with the number of tiles in flight.
+__device__ unsigned look_back_sum2(uint64_t* desc, uint64_t* gdesc, uint64_t* gacc, int64_t tile, int64_t ntiles,
+                                   unsigned total, uint32_t limit, unsigned* status, bool& gave_up) {
+  const int lane = lane_id();
+  gave_up = false;
+  const int64_t g = tile >> 5;
+  const int pos = (int)(tile & 31);
+  if (lane == 0) {
+    st_relaxed_u64(desc + tile, ((tile == 0 ? 2ull : 1ull) << 32) | total);
+    const int64_t gsize = min((int64_t)32, ntiles - (g << 5));
+    const unsigned long long old = atomicAdd(reinterpret_cast<unsigned long long*>(gacc + g), (1ull << 48) | total);
+    if ((int64_t)(old >> 48) + 1 == gsize)
+      atomicMax(reinterpret_cast<unsigned long long*>(gdesc + g), (1ull << 32) | (uint32_t)(old + total));
+  }
+  unsigned prefix = 0;
+  uint32_t polls = 0;
+  bool timed_out = false;
+  bool done = tile == 0;
+  if (!done && pos > 0) {  // own group: lane l holds position l < pos
+    const int64_t g0 = g << 5;
+    uint64_t d = lane < pos ? ld_relaxed_u64(desc + g0 + lane) : (1ull << 32);
+    unsigned pm;
+    int fl;
+    for (;;) {
+      pm = __ballot_sync(kFull, lane < pos && (d >> 32) == 2u);
+      fl = pm ? 31 - __clz(pm) : -1;
+      const bool missing = lane < pos && lane > fl && (d >> 32) == 0u;
+      if (!__any_sync(kFull, missing)) break;
+      if (++polls > limit) {
+        timed_out = true;
+        break;
+      }
+      if (polls > 64) __nanosleep(64);
+      if (missing) d = ld_relaxed_u64(desc + g0 + lane);
+    }
+    if (!__any_sync(kFull, timed_out)) {
+      unsigned v = (lane < pos && lane >= fl) ? (unsigned)d : 0u;
+      prefix = __reduce_add_sync(kFull, v);
+      done = fl >= 0;
+    }
+  }
+  if (!done && !__any_sync(kFull, timed_out)) {  // whole groups: lane l holds group gw - l
+    for (int64_t gw = g - 1;; gw -= 32) {
+      const int64_t gi = gw - lane;
+      uint64_t d = gi >= 0 ? ld_relaxed_u64(gdesc + gi) : (2ull << 32);  // before group 0: 0
+      unsigned pm;
+      for (;;) {
+        pm = __ballot_sync(kFull, (d >> 32) == 2u);
+        const int fl = pm ? __ffs(pm) - 1 : 32;
+        const bool missing = lane <= fl && (d >> 32) == 0u;
+        if (!__any_sync(kFull, missing)) break;
+        if (++polls > limit) {
+          timed_out = true;
+          break;
+        }
+        if (polls > 64) __nanosleep(64);
+        if (missing && gi >= 0) d = ld_relaxed_u64(gdesc + gi);
+      }
+      if (__any_sync(kFull, timed_out)) break;
+      const int fl = pm ? __ffs(pm) - 1 : 32;
+      prefix += __reduce_add_sync(kFull, lane <= fl ? (unsigned)d : 0u);
+      if (pm) break;
+    }
+  }
+  if (__any_sync(kFull, timed_out)) {
+    gave_up = true;
+    if (lane == 0) {
+      atomicOr(status, (unsigned)kDevTimeout);
+      st_relaxed_u64(desc + tile, (2ull << 32) | total);
+      if (pos == 31) atomicMax(reinterpret_cast<unsigned long long*>(gdesc + g), (2ull << 32) | total);
+    }
+    return 0u;
+  }
+  if (lane == 0) {
+    const uint64_t inc = (2ull << 32) | (uint32_t)(prefix + total);
+    if (tile != 0) st_relaxed_u64(desc + tile, inc);
+    if (pos == 31) atomicMax(reinterpret_cast<unsigned long long*>(gdesc + g), inc);
+  }
+  return prefix;
+}
+
 template <class R>
 __host__ __device__ constexpr int grid_scan_tile() {
   return R::kComp ? 8192 : 16384;
@@ -399,6 +489,16 @@ __global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ 
           st_release_u32(flags + tile, 2u);
         } else {
           st_relaxed_u64(agg + tile, (2ull << 32) | to_bits(R::ident()));
+          if constexpr (std::is_same<R, Plain<AddU>>::value) {  // keep the group level consistent
+            const int64_t ngroups = (ntiles + 31) / 32, g = tile >> 5;
+            const int64_t gsize = min((int64_t)32, ntiles - (g << 5));
+            uint64_t* gd = inc + ntiles;
+            const unsigned long long old =
+                atomicAdd(reinterpret_cast<unsigned long long*>(gd + ngroups + g), 1ull << 48);
+            if ((int64_t)(old >> 48) + 1 == gsize)
+              atomicMax(reinterpret_cast<unsigned long long*>(gd + g), (1ull << 32) | (uint32_t)old);
+            if ((tile & 31) == 31) atomicMax(reinterpret_cast<unsigned long long*>(gd + g), 2ull << 32);
+          }
         }
       }
       return;
@@ -463,8 +563,15 @@ __global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ 
     total = R::shfl_idx(total, 0, 32);
     bool gave_up;
     V prefix;
-    if constexpr (R::kComp) prefix = look_back_op<R>(flags, agg, inc, tile, total, limit, status, gave_up);
-    else prefix = look_back_packed<R>(agg, tile, total, limit, status, gave_up);
+    if constexpr (R::kComp) {
+      prefix = look_back_op<R>(flags, agg, inc, tile, total, limit, status, gave_up);
+    } else if constexpr (std::is_same<R, Plain<AddU>>::value) {
+      // group descriptors and accumulators after the tile slots
+      const int64_t ngroups = (ntiles + 31) / 32;
+      prefix = look_back_sum2(agg, inc + ntiles, inc + ntiles + ngroups, tile, ntiles, total, limit, status, gave_up);
+    } else {
+      prefix = look_back_packed<R>(agg, tile, total, limit, status, gave_up);
+    }
     if (lane == 0) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) s_cp[k] = R::op(prefix, s_cp[k]);
@@ -600,7 +707,7 @@ static cox_status launch_scan_scope(cox_scope scope, int block, const void* d_in
   }
   if (n >= 32 && n / 32 < (int64_t(1) << 31) && aligned16(d_in) && aligned16(d_out)) {
     const int64_t ntiles = (n + kGridRowsTile * 32 - 1) / (kGridRowsTile * 32);
-    const size_t need = scan_ws_bytes(ntiles);
+    const size_t need = scan_ws_bytes(ntiles) + 16 * (size_t)((ntiles + 31) / 32);  // + group words (sums)
     if (!ws || ws_bytes < need) return COX_ENOMEM;
     if (!aligned16(ws)) return COX_EINVAL;
     CUtensorMap tin, tout;
@@ -643,7 +750,8 @@ using namespace cox;
 
 extern "C" size_t cox_scan_workspace(cox_scope scope, int64_t n) {
   if (scope != COX_SCOPE_GRID || n <= 0) return 0;
-  return scan_ws_bytes((n + 8191) / 8192);  // enough for either tile size
+  const int64_t t = (n + 8191) / 8192;  // enough for either tile size, plus group words
+  return scan_ws_bytes(t) + 16 * (size_t)((t + 31) / 32);
 }
 
 extern "C" cox_status cox_scan(cox_op op, cox_dtype dt, cox_scope scope, int block_dim, const void* d_in, void* d_out,
