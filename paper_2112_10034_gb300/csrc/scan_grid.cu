@@ -299,6 +299,143 @@ __device__ unsigned look_back_sum2(uint64_t* desc, uint64_t* gdesc, uint64_t* ga
   return prefix;
 }
 
+// Two-level look-back for any scan value (pairs included).  Per tile: a
+// flag (1 aggregate, 2 inclusive prefix) and the two value slots of
+// look_back_op.  Per group of 32 tiles: an arrival counter, a flag and the
+// same two slots.  The tile whose arrival completes its group folds the
+// group's 32 aggregates (in tile order, so the group value does not depend
+// on arrival order) and publishes the group aggregate; the group's last
+// tile publishes its inclusive prefix as the group's.  The look-back reads
+// the tile's own group, then whole groups, 32 per window.  Called by a
+// whole warp; returns the exclusive prefix.
+struct GroupWs {
+  uint32_t* gflag;
+  uint32_t* gcnt;
+  uint64_t* gagg;
+  uint64_t* ginc;
+};
+
+template <class R>
+__device__ typename R::V look_back_op2(uint32_t* flags, uint64_t* agg, uint64_t* inc, GroupWs gw, int64_t tile,
+                                       int64_t ntiles, typename R::V total, uint32_t limit, unsigned* status,
+                                       bool& gave_up) {
+  using V = typename R::V;
+  const int lane = lane_id();
+  gave_up = false;
+  const int64_t g = tile >> 5;
+  const int pos = (int)(tile & 31);
+  const int64_t g0 = g << 5;
+  // ---- publish the aggregate; the group's completing tile publishes the group's
+  if (lane == 0) {
+    if (tile == 0) {
+      st_relaxed_u64(inc, pack<R>(total));
+      st_relaxed_u64(agg, pack<R>(total));
+      st_release_u32(flags, 2u);
+    } else {
+      st_relaxed_u64(agg + tile, pack<R>(total));
+      st_release_u32(flags + tile, 1u);
+    }
+  }
+  int last = 0;
+  if (lane == 0) {
+    __threadfence();
+    const int64_t gsize = min((int64_t)32, ntiles - g0);
+    last = (int64_t)atomicAdd(gw.gcnt + g, 1u) + 1 == gsize;
+    if (last) __threadfence();
+  }
+  if (__shfl_sync(kFull, last, 0)) {
+    const int64_t gsize = min((int64_t)32, ntiles - g0);
+    V v = lane < gsize ? unpack<R>(ld_relaxed_u64(agg + g0 + lane)) : R::ident();
+    v = warp_fold<R>(v);
+    if (lane == 0) {
+      st_relaxed_u64(gw.gagg + g, pack<R>(v));
+      __threadfence();
+      atomicCAS(gw.gflag + g, 0u, 1u);  // a published inclusive prefix (2) stays
+    }
+  }
+  V prefix = R::ident();
+  uint32_t polls = 0;
+  bool timed_out = false;
+  bool done = tile == 0;
+  if (!done && pos > 0) {  // own group: lane l holds position l < pos
+    uint32_t f = lane < pos ? ld_acquire_u32(flags + g0 + lane) : 1u;
+    unsigned pm;
+    int fl;
+    for (;;) {
+      pm = __ballot_sync(kFull, lane < pos && f == 2u);
+      fl = pm ? 31 - __clz(pm) : -1;
+      const bool missing = lane < pos && lane > fl && f == 0u;
+      if (!__any_sync(kFull, missing)) break;
+      if (++polls > limit) {
+        timed_out = true;
+        break;
+      }
+      if (polls > 64) __nanosleep(64);
+      if (missing) f = ld_acquire_u32(flags + g0 + lane);
+    }
+    if (!__any_sync(kFull, timed_out)) {
+      V part = R::ident();
+      if (lane < pos && lane >= fl) part = unpack<R>(ld_relaxed_u64((lane == fl ? inc : agg) + g0 + lane));
+      prefix = warp_fold<R>(part);
+      done = fl >= 0;
+    }
+  }
+  if (!done && !__any_sync(kFull, timed_out)) {  // whole groups: lane l holds group gw0 - l
+    V gsum = R::ident();
+    for (int64_t gw0 = g - 1;; gw0 -= 32) {
+      const int64_t gi = gw0 - lane;
+      uint32_t f = gi >= 0 ? ld_acquire_u32(gw.gflag + gi) : 2u;  // before group 0: the identity
+      unsigned pm;
+      for (;;) {
+        pm = __ballot_sync(kFull, f == 2u);
+        const int fl = pm ? __ffs(pm) - 1 : 32;
+        const bool missing = lane <= fl && f == 0u;
+        if (!__any_sync(kFull, missing)) break;
+        if (++polls > limit) {
+          timed_out = true;
+          break;
+        }
+        if (polls > 64) __nanosleep(64);
+        if (missing && gi >= 0) f = ld_acquire_u32(gw.gflag + gi);
+      }
+      if (__any_sync(kFull, timed_out)) break;
+      const int fl = pm ? __ffs(pm) - 1 : 32;
+      V part = R::ident();
+      if (lane <= fl && gi >= 0) part = unpack<R>(ld_relaxed_u64((f == 2u ? gw.ginc : gw.gagg) + gi));
+      gsum = R::op(warp_fold<R>(part), gsum);  // older windows on the left
+      if (pm) break;
+    }
+    prefix = R::op(gsum, prefix);
+  }
+  if (__any_sync(kFull, timed_out)) {
+    gave_up = true;
+    if (lane == 0) {
+      atomicOr(status, (unsigned)kDevTimeout);
+      st_relaxed_u64(inc + tile, pack<R>(total));  // release successors
+      st_release_u32(flags + tile, 2u);
+      if (pos == 31) {
+        st_relaxed_u64(gw.ginc + g, pack<R>(total));
+        __threadfence();
+        atomicMax(gw.gflag + g, 2u);
+      }
+    }
+    return R::ident();
+  }
+  if (lane == 0) {
+    const V incl = R::op(prefix, total);
+    if (tile != 0) {
+      st_relaxed_u64(inc + tile, pack<R>(incl));
+      st_release_u32(flags + tile, 2u);
+    }
+    if (pos == 31) {
+      st_relaxed_u64(gw.ginc + g, pack<R>(incl));
+      __threadfence();
+      atomicMax(gw.gflag + g, 2u);
+    }
+  }
+  return prefix;
+}
+
 template <class R>
 __host__ __device__ constexpr int grid_scan_tile() {
   return R::kComp ? 8192 : 16384;
@@ -484,9 +621,21 @@ __global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ 
       if (tid == 0) {
         atomicOr(status, (unsigned)kDevTimeout);
         mbar_wait_bounded(&s_bar, 0u, limit);
-        if constexpr (R::kComp) {
+        if constexpr (!std::is_same<R, Plain<AddU>>::value) {
           st_relaxed_u64(inc + tile, pack<R>(R::ident()));
+          st_relaxed_u64(agg + tile, pack<R>(R::ident()));
           st_release_u32(flags + tile, 2u);
+          // group level: count this tile's arrival; the group slots then hold a partial fold, and the
+          // device status already says the results are not to be used
+          const int64_t ngroups = (ntiles + 31) / 32;
+          uint64_t* ginc = inc + ntiles;
+          uint32_t* gflag = reinterpret_cast<uint32_t*>(ginc + 2 * ngroups);
+          atomicAdd(gflag + ngroups + (tile >> 5), 1u);
+          if ((tile & 31) == 31) {
+            st_relaxed_u64(ginc + (tile >> 5), pack<R>(R::ident()));
+            __threadfence();
+            atomicMax(gflag + (tile >> 5), 2u);
+          }
         } else {
           st_relaxed_u64(agg + tile, (2ull << 32) | to_bits(R::ident()));
           if constexpr (std::is_same<R, Plain<AddU>>::value) {  // keep the group level consistent
@@ -563,14 +712,18 @@ __global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ 
     total = R::shfl_idx(total, 0, 32);
     bool gave_up;
     V prefix;
-    if constexpr (R::kComp) {
-      prefix = look_back_op<R>(flags, agg, inc, tile, total, limit, status, gave_up);
-    } else if constexpr (std::is_same<R, Plain<AddU>>::value) {
+    const int64_t ngroups = (ntiles + 31) / 32;
+    if constexpr (std::is_same<R, Plain<AddU>>::value) {
       // group descriptors and accumulators after the tile slots
-      const int64_t ngroups = (ntiles + 31) / 32;
       prefix = look_back_sum2(agg, inc + ntiles, inc + ntiles + ngroups, tile, ntiles, total, limit, status, gave_up);
     } else {
-      prefix = look_back_packed<R>(agg, tile, total, limit, status, gave_up);
+      // group slots after the tile slots: ginc, gagg (64-bit), then gflag, gcnt (32-bit)
+      GroupWs gw;
+      gw.ginc = inc + ntiles;
+      gw.gagg = gw.ginc + ngroups;
+      gw.gflag = reinterpret_cast<uint32_t*>(gw.gagg + ngroups);
+      gw.gcnt = gw.gflag + ngroups;
+      prefix = look_back_op2<R>(flags, agg, inc, gw, tile, ntiles, total, limit, status, gave_up);
     }
     if (lane == 0) {
 #pragma unroll
@@ -707,7 +860,7 @@ static cox_status launch_scan_scope(cox_scope scope, int block, const void* d_in
   }
   if (n >= 32 && n / 32 < (int64_t(1) << 31) && aligned16(d_in) && aligned16(d_out)) {
     const int64_t ntiles = (n + kGridRowsTile * 32 - 1) / (kGridRowsTile * 32);
-    const size_t need = scan_ws_bytes(ntiles) + 16 * (size_t)((ntiles + 31) / 32);  // + group words (sums)
+    const size_t need = scan_ws_bytes(ntiles) + 24 * (size_t)((ntiles + 31) / 32);  // + group words
     if (!ws || ws_bytes < need) return COX_ENOMEM;
     if (!aligned16(ws)) return COX_EINVAL;
     CUtensorMap tin, tout;
@@ -751,7 +904,7 @@ using namespace cox;
 extern "C" size_t cox_scan_workspace(cox_scope scope, int64_t n) {
   if (scope != COX_SCOPE_GRID || n <= 0) return 0;
   const int64_t t = (n + 8191) / 8192;  // enough for either tile size, plus group words
-  return scan_ws_bytes(t) + 16 * (size_t)((t + 31) / 32);
+  return scan_ws_bytes(t) + 24 * (size_t)((t + 31) / 32);
 }
 
 extern "C" cox_status cox_scan(cox_op op, cox_dtype dt, cox_scope scope, int block_dim, const void* d_in, void* d_out,
