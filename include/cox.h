@@ -244,11 +244,13 @@ cox_status cox_coalesced(cox_cgfn fn, cox_dtype dt, int block_dim, const void* d
  * through a warp-aggregated atomic: each coalesced group of keeping lanes
  * gets one contiguous range of d_out from an atomic add on *d_count, and a
  * lane's slot is its group rank in it.  A warp aggregates its 16 rounds of
- * 32 keys into one atomic.  The ORDER of the ranges is the order in which
+ * 32 keys, and a CTA its 8 warps, into one atomic.  The ORDER of the ranges is the order in which
  * the atomics landed (not deterministic); the kept keys, their count, and
  * the lane order inside each group are.  d_out: room for n keys; d_count:
  * one int64, zeroed by the call, holds the count when the stream reaches
- * the end of the call.  dt: COX_I32 or COX_U32.
+ * the end of the call.  dt: COX_I32 or COX_U32.  Keys arrive in 16 KB
+ * chunks by TMA bulk copies (16-byte aligned d_keys); a copy that does not
+ * land within the spin limit records COX_ETIMEOUT for cox_device_status().
  */
 cox_status cox_filter_aggregated(cox_dtype dt, const void* d_keys, int64_t n, int64_t threshold, void* d_out,
                                  int64_t* d_count, void* stream);
@@ -273,11 +275,15 @@ cox_status cox_vote_stats(cox_dtype dt, int width, const void* d_pred, int64_t n
  * the SDK's shfl_intimage_rows + shfl_vertical_shfl pair (Table 1).
  * in_dt: COX_U8 (uint8 pixels) or COX_U32 / COX_I32 (32-bit, summed mod
  * 2^32).  d_out: batch*height*width uint32.  d_workspace:
- * cox_integral_image_workspace() bytes (per image row the prefix of each
- * 32-pixel strip; per image, band of 64 rows and column a band prefix),
- * 16-byte aligned.  Strip prefixes per row, band column sums and their
- * prefixes, then one warp per (image, band, 32-column strip) walks the
- * band's rows (shuffle row scan plus the strip prefix, running column sums).
+ * cox_integral_image_workspace() bytes (per image row a word per 32-pixel
+ * strip; per image, band of 64 rows and column a word; per image, band and
+ * 128 columns a word), 16-byte aligned.  Rows are cut into bands of 64 and
+ * strips; per (image, band, strip) one warp first sums its block (row
+ * totals, column prefixes, block total), then one warp walks the band's
+ * rows from the integral above it (row scan plus the row's prefix left of
+ * the strip, running column sums).  16-byte aligned input and output whose
+ * rows are whole 16-byte units read the pixels twice; other layouts take a
+ * three-pass form that reads them three times.
  */
 cox_status cox_integral_image(cox_dtype in_dt, int64_t batch, int64_t height, int64_t width, const void* d_in,
                               uint32_t* d_out, void* d_workspace, size_t workspace_bytes, void* stream);
@@ -298,8 +304,9 @@ size_t cox_integral_image_workspace(int64_t batch, int64_t height, int64_t width
  *   unless flags has COX_F_WS_READY, in which case the caller guarantees those
  *   bytes are zero.  Not shared across concurrent calls.
  *   flags: 0 or COX_F_WS_READY.
- * Tiles of 16384 keys (one CTA of block_dim threads each; block_dim only
- * shapes the launch) are ordered by a ticket counter; each tile's look-back
+ * Tiles of 16384 keys (one CTA of 256 threads each, whatever block_dim: the
+ * result does not depend on the block size, which is only validated) are
+ * ordered by a ticket counter; each tile's look-back
  * polls its predecessors' descriptors.  A poll that exceeds the spin
  * limit (cox_set_spin_limit) gives up: the tile publishes a zero prefix, writes
  * nothing, and COX_ETIMEOUT is recorded for cox_device_status().  Every write

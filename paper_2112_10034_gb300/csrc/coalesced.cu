@@ -7,7 +7,9 @@
 // active lanes then run the warp intrinsics with that member mask
 // (shfl.sync / vote.sync / redux.sync with a partial mask), exactly as a
 // coalesced_group does.  Group ranks are popc(mask & lanemask_lt); the lane
-// of rank k is found by a 5-step binary search over popc prefixes.  The
+// of rank k is found by a 5-step binary search over popc prefixes, and the
+// group ballot is an OR-reduction of each member's vote shifted to its
+// rank.  The
 // integer group scan alone runs over the full warp with inactive lanes
 // contributing 0 (the same sums, exactly).
 #include "cox_common.cuh"
@@ -15,7 +17,8 @@
 
 namespace cox {
 
-// Lane of the k-th (0-based) set bit of mask; k < popc(mask).
+// Lane of the k-th (0-based) set bit of mask; k < popc(mask).  (A 5-step
+// binary search over popc prefixes measured faster than __fns here.)
 __device__ __forceinline__ int nth_set_lane(unsigned mask, int k) {
   int pos = 0;
 #pragma unroll
@@ -44,25 +47,19 @@ __device__ __forceinline__ uint32_t group_fn(int fn, uint32_t v, unsigned mask, 
     case COX_CG_SHFL_UP: return __shfl_sync(mask, v, rank >= param ? nth_set_lane(mask, rank - param) : lane);
     case COX_CG_SHFL_DOWN:
       return __shfl_sync(mask, v, rank + param < size ? nth_set_lane(mask, rank + param) : lane);
-    case COX_CG_BALLOT: {
-      const unsigned b = __ballot_sync(mask, vote_pred<DT>(v));
-      uint32_t r = 0;
-      unsigned m = mask;
-      for (int k = 0; m; ++k, m &= m - 1u)  // bit k = the k-th member's vote
-        if (b & (m & (0u - m))) r |= 1u << k;
-      return r;
-    }
+    case COX_CG_BALLOT:  // bit k = the vote of rank k: each member ORs its vote in at its rank
+      return __reduce_or_sync(mask, (vote_pred<DT>(v) ? 1u : 0u) << rank);
     case COX_CG_ANY: return __any_sync(mask, vote_pred<DT>(v)) ? 1u : 0u;
     case COX_CG_ALL: return __all_sync(mask, vote_pred<DT>(v)) ? 1u : 0u;
     default: return __reduce_add_sync(mask, v);  // COX_CG_REDUCE_SUM
   }
 }
 
-// Persistent warps take 4 consecutive 32-element groups at a time, their
+// Persistent warps take 8 consecutive 32-element groups at a time, their
 // loads issued together.  SCAN_SUM (integers, exact) runs as a full-warp
 // Hillis-Steele scan in which inactive lanes contribute 0: an active lane's
 // inclusive prefix over the lanes up to it is its group's prefix by rank.
-constexpr int kCgUnroll = 4;
+constexpr int kCgUnroll = 8;
 
 template <int DT>
 __global__ void __launch_bounds__(256) k_coalesced(int fn, const uint32_t* __restrict__ in,
@@ -103,41 +100,103 @@ __global__ void __launch_bounds__(256) k_coalesced(int fn, const uint32_t* __res
 
 // filter_arr with warp-aggregated slots.  A warp takes 16 rounds of 32 keys
 // (round j: keys base + 32j + lane); round j's group is its keeping lanes.
-// One atomic per warp reserves the 16 groups' total; group j's range starts
-// after groups 0 .. j-1, and a lane's slot is base + that offset + its rank.
+// Group j's range starts after groups 0 .. j-1 of the warp, and a lane's
+// slot is the warp's base + that offset + its rank.  The warps of a CTA
+// aggregate once more: one atomic per CTA per chunk of 8 x 512 keys
+// reserves the warps' totals, and warp w's base follows warps 0 .. w-1.
+// Chunks (16 KB) reach shared memory by TMA bulk copies, two ahead of the
+// one being processed.
 constexpr int kFilterRounds = 16;
+constexpr int kFilterWarps = 8;
+constexpr int kFilterStages = 3;
+constexpr int kFilterChunk = 32 * kFilterRounds * kFilterWarps;  // keys per CTA iteration
+constexpr size_t kFilterSmem = (size_t)kFilterStages * kFilterChunk * sizeof(uint32_t);
 
 template <bool SIGNED>
-__global__ void __launch_bounds__(256) k_filter_aggregated(const uint32_t* __restrict__ keys, int64_t n,
-                                                           KeepRule rule, uint32_t* __restrict__ out,
-                                                           unsigned long long* __restrict__ count) {
-  const int lane = lane_id();
+__global__ void __launch_bounds__(32 * kFilterWarps, 4)
+    k_filter_aggregated(const uint32_t* __restrict__ keys, int64_t n, KeepRule rule, uint32_t* __restrict__ out,
+                        unsigned long long* __restrict__ count, uint32_t limit, unsigned* status, int vec) {
+  extern __shared__ __align__(16) uint32_t fbuf[];
+  __shared__ __align__(8) uint64_t bar[kFilterStages];
+  __shared__ unsigned s_tot[2][kFilterWarps];  // by iteration parity: a warp runs at most one iteration ahead
+  __shared__ unsigned long long s_base[2];
+  const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   const unsigned lt = lanemask_lt();
-  constexpr int64_t CH = 32 * kFilterRounds;
-  const int64_t nch = (n + CH - 1) / CH;
-  const int64_t wstep = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nch; c += wstep) {
-    const int64_t base = c * CH;
-    uint32_t k[kFilterRounds];
-    unsigned m[kFilterRounds];
-#pragma unroll
-    for (int j = 0; j < kFilterRounds; ++j) {
-      const int64_t i = base + 32 * j + lane;
-      k[j] = i < n ? __ldcs(keys + i) : 0u;
-      m[j] = __ballot_sync(kFull, i < n && keep_key<SIGNED>(k[j], rule));
+  const int64_t nch = (n + kFilterChunk - 1) / kFilterChunk;
+  const int64_t nfull = vec ? n / kFilterChunk : 0;  // chunks that arrive by bulk copy
+  const int64_t G = gridDim.x;
+  auto issue = [&](int64_t j) {  // thread 0: this CTA's iteration j into slot j % stages
+    const int64_t c = blockIdx.x + j * G;
+    if (c < nfull) {
+      uint64_t* b = bar + (int)(j % kFilterStages);
+      mbar_arrive_expect_tx(b, kFilterChunk * 4);
+      tma_load_1d(fbuf + (j % kFilterStages) * kFilterChunk, keys + c * kFilterChunk, kFilterChunk * 4, b);
     }
+  };
+  if (tid == 0) {
+    for (int s = 0; s < kFilterStages; ++s) mbar_init(bar + s, 1);
+    mbar_init_fence();
+    for (int j = 0; j < kFilterStages - 1; ++j) issue(j);
+  }
+  __syncthreads();
+  bool ok = true;
+  int64_t it = 0;
+  for (int64_t c = blockIdx.x; c < nch; c += G, ++it) {
+    // slot (it - 1) % stages was read last iteration, before its barriers
+    if (tid == 0) issue(it + kFilterStages - 1);
+    const int par = (int)(it & 1);
+    const int64_t base = c * kFilterChunk + wib * (32 * kFilterRounds);  // this warp's keys
+    uint32_t k[kFilterRounds];
+    if (c < nfull) {
+      const int slot = (int)(it % kFilterStages);
+      ok = mbar_wait_bounded(bar + slot, (uint32_t)((it / kFilterStages) & 1), limit);
+      if (__syncthreads_or(!ok)) {
+        ok = false;
+        break;
+      }
+      const uint32_t* src = fbuf + slot * kFilterChunk + wib * (32 * kFilterRounds);
+#pragma unroll
+      for (int j = 0; j < kFilterRounds; ++j) k[j] = src[32 * j + lane];
+    } else {
+#pragma unroll
+      for (int j = 0; j < kFilterRounds; ++j) {
+        const int64_t i = base + 32 * j + lane;
+        k[j] = i < n ? __ldcs(keys + i) : 0u;
+      }
+    }
+    const int rem = (int)max((int64_t)0, min(n - base, (int64_t)(32 * kFilterRounds)));  // this warp's valid keys
+    unsigned m[kFilterRounds];
     unsigned total = 0;
 #pragma unroll
-    for (int j = 0; j < kFilterRounds; ++j) total += __popc(m[j]);
-    unsigned long long b = 0;
-    if (lane == 0 && total) b = atomicAdd(count, (unsigned long long)total);
-    b = __shfl_sync(kFull, b, 0);
+    for (int j = 0; j < kFilterRounds; ++j) {
+      m[j] = __ballot_sync(kFull, 32 * j + lane < rem && keep_key<SIGNED>(k[j], rule));
+      total += __popc(m[j]);
+    }
+    if (lane == 0) s_tot[par][wib] = total;
+    fence_proxy_async_smem();  // this thread's reads of the slot, before the refill's async writes
+    __syncthreads();
+    if (tid == 0) {
+      unsigned sum = 0;
+#pragma unroll
+      for (int w = 0; w < kFilterWarps; ++w) sum += s_tot[par][w];
+      s_base[par] = sum ? atomicAdd(count, (unsigned long long)sum) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long b = s_base[par];
+    for (int w = 0; w < wib; ++w) b += s_tot[par][w];
+    uint32_t* o = out + b;  // this warp's range
     unsigned off = 0;
 #pragma unroll
     for (int j = 0; j < kFilterRounds; ++j) {
-      if (m[j] & (1u << lane)) out[b + off + __popc(m[j] & lt)] = k[j];
+      if (m[j] & (1u << lane)) o[off + __popc(m[j] & lt)] = k[j];
       off += __popc(m[j]);
     }
+  }
+  if (!ok && tid == 0) {  // a copy did not land in time: record it, give the copies in flight a bounded wait
+    atomicOr(status, (unsigned)kDevTimeout);
+    for (int64_t j = it; j < it + kFilterStages; ++j)  // iterations it .. it + stages - 1 were issued
+      if (blockIdx.x + j * G < nfull)
+        mbar_wait_bounded(bar + (int)(j % kFilterStages), (uint32_t)((j / kFilterStages) & 1), limit);
   }
 }
 
@@ -158,12 +217,15 @@ static cox_status launch_filter(const void* d_keys, int64_t n, int64_t threshold
                                 cudaStream_t st) {
   auto k = k_filter_aggregated<SIGNED>;
   static int g = 0;
-  if (g == 0) g = persistent_grid(k, 256, 0, 1 << 30);
-  const int64_t chunks = (n + 32 * kFilterRounds - 1) / (32 * kFilterRounds);
-  const int64_t ctas = (chunks + 7) / 8;
-  k<<<(int)(ctas < g ? ctas : g), 256, 0, st>>>(static_cast<const uint32_t*>(d_keys), n, keep_rule<SIGNED>(threshold),
-                                                static_cast<uint32_t*>(d_out),
-                                                reinterpret_cast<unsigned long long*>(d_count));
+  if (g == 0) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFilterSmem) != cudaSuccess)
+      return COX_ECUDA;
+    g = persistent_grid(k, 32 * kFilterWarps, kFilterSmem, 1 << 30);
+  }
+  const int64_t ctas = (n + kFilterChunk - 1) / kFilterChunk;
+  k<<<(int)(ctas < g ? ctas : g), 32 * kFilterWarps, kFilterSmem, st>>>(
+      static_cast<const uint32_t*>(d_keys), n, keep_rule<SIGNED>(threshold), static_cast<uint32_t*>(d_out),
+      reinterpret_cast<unsigned long long*>(d_count), spin_limit(), device_status_word(), aligned16(d_keys) ? 1 : 0);
   return launch_status();
 }
 

@@ -1,8 +1,10 @@
 // cox_ballot_compact: stable stream compaction from warp ballots.
 //
 // One CTA per tile of 16384 keys (64 KB), taken from an atomic ticket in the
-// order CTAs start; the CTA's B threads cover the tile in 16384 / (16 B)
-// passes of 16 keys each (4 passes at B = 256, 1 at B = 1024).  The tile arrives in shared memory by one
+// order CTAs start; the CTA's 256 threads cover the tile in 4 passes of 16
+// keys each (the result does not depend on the caller's block size, so
+// every launch takes the shape that keeps three tiles in flight per SM --
+// 1024-thread CTAs fit two per SM and ran ~2x slower).  The tile arrives in shared memory by one
 // TMA bulk copy (plain loads for a ragged or unaligned tile), so keys never
 // occupy registers and three 64 KB tiles fit in flight per SM -- a tile's
 // chain of round trips (ticket, copy, look-back) is what bounds this op, and
@@ -29,8 +31,10 @@
 
 namespace cox {
 
+constexpr int kCompactThreads = 256;
+
 template <bool SIGNED>
-__global__ void __launch_bounds__(1024) k_ballot_compact(const uint32_t* __restrict__ keys, int64_t n,
+__global__ void __launch_bounds__(kCompactThreads, 3) k_ballot_compact(const uint32_t* __restrict__ keys, int64_t n,
                                                          int64_t thr, uint32_t* __restrict__ out,
                                                          int64_t* __restrict__ d_count, unsigned* ticket,
                                                          uint64_t* desc, int64_t ntiles, uint32_t limit,
@@ -113,7 +117,7 @@ extern "C" cox_status cox_ballot_compact(cox_dtype dt, int width, int block_dim,
   auto launch = [&](auto kern) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return COX_ECUDA;
-    kern<<<(unsigned)ntiles, block_dim, smem, st>>>(static_cast<const uint32_t*>(d_keys), n, threshold,
+    kern<<<(unsigned)ntiles, kCompactThreads, smem, st>>>(static_cast<const uint32_t*>(d_keys), n, threshold,
                                                   static_cast<uint32_t*>(d_out), d_count, ticket, desc, ntiles,
                                                   spin_limit(), device_status_word(), vec);
     return launch_status();

@@ -554,6 +554,28 @@ __device__ __forceinline__ void row_ring(const CUtensorMap* tin, const CUtensorM
   __syncwarp();
 }
 
+// ------------------------------------------------ one tile row per lane
+// The same Hillis-Steele combines with each width-W tile collapsed into one
+// thread -- the paper's intra-warp loop (Section 2.3, Code 3), applied on
+// the GPU: lane t of a warp holds row t (32 consecutive elements, 32/W
+// tiles) of the warp's 1024-element chunk, and step d sets
+// x[i] = x[i-d] op x[i] for rank i from W-1 down to d, so x[i-d] still holds
+// the previous step's value, exactly as the shuffle's source lane does.
+// Same operands in the same order, hence the same bits, with no shuffles,
+// selects or idle lanes.
+template <class R, int W>
+__device__ __forceinline__ void scan_row_regs(typename R::V (&v)[32]) {
+#pragma unroll
+  for (int t0 = 0; t0 < 32; t0 += W) {
+#pragma unroll
+    for (int i = W - 1; i >= 1; --i) v[t0 + i] = R::op_fresh(v[t0 + i - 1], v[t0 + i]);
+#pragma unroll
+    for (int d = 2; d < W; d <<= 1)
+#pragma unroll
+      for (int i = W - 1; i >= d; --i) v[t0 + i] = R::op(v[t0 + i - d], v[t0 + i]);
+  }
+}
+
 // ------------------------------------------------------------ host helpers
 // Tensor map of a 32-bit array viewed as `rows` rows of 32 elements (128 B),
 // boxes of 32 x `box_rows`, 128-byte swizzle: in shared memory the 16-byte

@@ -119,35 +119,33 @@ __device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, const uint32_t* b
 }
 
 // ------------------------------------------------------------------ scan
-// Warp w scans rows 64 w .. 64 w + 63 of the tile (row r = elements 32 r ..
-// 32 r + 31), eight at a time, by Hillis-Steele at width W, in place.
+// Thread t scans rows t and t + 256 of the tile (row r = elements 32 r ..
+// 32 r + 31) in registers, each width-W tile collapsed into the thread
+// (scan_row_regs), in place.  The tile is linear in shared memory (one 1D
+// bulk copy per request tile), so a lane's 16-byte reads of its row meet
+// 8-way bank conflicts; the tile's arithmetic, not shared memory, bounds it.
 template <class R, int W>
 __device__ void serve_scan_rows(uint32_t* buf) {
   using T = typename R::T;
   using V = typename R::V;
-  const int lane = lane_id(), warp = threadIdx.x >> 5;
-  const int rank = lane & (W - 1);
-  constexpr int RPW = (int)(kTile / 32 / (kServeBlock / 32));
+  uint4* b4 = reinterpret_cast<uint4*>(buf);
 #pragma unroll 1
-  for (int g = 0; g < RPW / 8; ++g) {
-    V v[8];
+  for (int h = 0; h < (int)(kTile / 32 / kServeBlock); ++h) {
+    const int r = h * kServeBlock + threadIdx.x;
+    V v[32];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = R::load(from_bits<T>(buf[(warp * RPW + g * 8 + i) * 32 + lane]));
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const V u = R::shfl_up_fresh(v[i], 1, W);
-      if (rank >= 1) v[i] = R::op_fresh(u, v[i]);
+    for (int j = 0; j < 8; ++j) {
+      const uint4 q = b4[r * 8 + j];
+      v[4 * j] = R::load(from_bits<T>(q.x));
+      v[4 * j + 1] = R::load(from_bits<T>(q.y));
+      v[4 * j + 2] = R::load(from_bits<T>(q.z));
+      v[4 * j + 3] = R::load(from_bits<T>(q.w));
     }
+    scan_row_regs<R, W>(v);
 #pragma unroll
-    for (int dd = 2; dd < W; dd <<= 1) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const V u = R::shfl_up(v[i], dd, W);
-        if (rank >= dd) v[i] = R::op(u, v[i]);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) buf[(warp * RPW + g * 8 + i) * 32 + lane] = to_bits(R::out(v[i]));
+    for (int j = 0; j < 8; ++j)
+      b4[r * 8 + j] = make_uint4(to_bits(R::out(v[4 * j])), to_bits(R::out(v[4 * j + 1])),
+                                 to_bits(R::out(v[4 * j + 2])), to_bits(R::out(v[4 * j + 3])));
   }
 }
 

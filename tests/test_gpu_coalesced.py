@@ -75,7 +75,7 @@ def test_coalesced_bad_arguments(cox):
 
 
 @pytest.mark.parametrize("d", [0.0, 0.1, 0.5, 0.9, 1.0])
-@pytest.mark.parametrize("n", [1, 1000, 70_001, (1 << 22) + 5])
+@pytest.mark.parametrize("n", [1, 1000, 4096, 70_001, 4096 * 37, (1 << 22) + 5])
 def test_filter_aggregated(cox, d, n):
     import torch
     # distinct keys (a shuffled range), so every output key names its input slot
@@ -114,3 +114,23 @@ def test_filter_unsigned_threshold_clamp(cox):
         kept, c = o.filter_multiset(o.U32, keys, t)
         assert int(cnt.item()) == c
         np.testing.assert_array_equal(np.sort(out.cpu().numpy()[:c].view(np.uint32).astype(np.int64)), kept)
+
+
+@pytest.mark.parametrize("n", [4096 * 5, 70_001])
+def test_filter_unaligned_keys(cox, n):
+    """Keys off the 16-byte grid take plain loads; the result is the same."""
+    import torch
+    keys = np.random.default_rng(n + 1).permutation(n).astype(np.int32)
+    t = n // 3
+    d_keys = torch.zeros(n + 4, dtype=torch.int32, device="cuda")
+    d_keys[1:n + 1] = dev(keys)
+    out = torch.full((n + 16,), POISON, dtype=torch.int32, device="cuda")
+    cnt = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    assert cox.cox_filter_aggregated(o.I32, d_keys.data_ptr() + 4, n, t, out.data_ptr(), cnt.data_ptr(), None) == 0
+    kept, want_c = o.filter_multiset(o.I32, keys, t)
+    c = int(cnt.item())
+    assert c == want_c
+    got = out.cpu().numpy()
+    np.testing.assert_array_equal(np.sort(got[:c].astype(np.int64)), kept)
+    assert (got[c:] == POISON).all()
+    assert cox.cox_device_status(None) == 0

@@ -60,7 +60,8 @@ def test_vote_stats_fp32_zeros_and_bad_args(cox):
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 7, 5), (3, 33, 31), (2, 64, 64), (4, 100, 1000),
-                                   (2, 1080, 1920), (1, 17, 4097)])
+                                   (2, 1080, 1920), (1, 17, 4097), (3, 130, 1040), (1, 700, 2048),
+                                   (2, 65, 16), (2, 3, 132), (1, 64, 528), (5, 129, 4)])
 @pytest.mark.parametrize("dt", ["u8", "u32"])
 def test_integral_image(cox, shape, dt):
     import torch
@@ -76,3 +77,27 @@ def test_integral_image(cox, shape, dt):
     got = out.cpu().numpy()
     np.testing.assert_array_equal(got[:b * h * w].view(np.uint32).reshape(shape), o.integral_image(img))
     assert (got[b * h * w:] == 0x7FBADBAD).all()
+
+
+@pytest.mark.parametrize("dt", ["u8", "u32"])
+@pytest.mark.parametrize("in_off,out_off", [(1, 0), (0, 1), (4, 2)])
+def test_integral_image_misaligned(cox, dt, in_off, out_off):
+    """Input or output off the 16-byte grid takes the three-pass form."""
+    import torch
+    b, h, w = 2, 70, 1040
+    bits = inputs.bits_u32(b * h * w, seed=77 + in_off)
+    img = (bits & 0xFF).astype(np.uint8).reshape(b, h, w) if dt == "u8" else bits.reshape(b, h, w)
+    code = cox.COX_U8 if dt == "u8" else cox.COX_U32
+    esz = 1 if dt == "u8" else 4
+    raw = img.view(np.uint8).ravel()
+    d_in = torch.zeros(raw.size + 64, dtype=torch.uint8, device="cuda")
+    d_in[in_off * esz:in_off * esz + raw.size] = torch.from_numpy(raw).cuda()
+    out = torch.full((b * h * w + 16,), 0x7FBADBAD, dtype=torch.int32, device="cuda")
+    wsb = cox.cox_integral_image_workspace(b, h, w)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    assert cox.cox_integral_image(code, b, h, w, d_in.data_ptr() + in_off * esz, out.data_ptr() + 4 * out_off,
+                                  ws.data_ptr(), wsb, None) == 0
+    got = out.cpu().numpy()
+    np.testing.assert_array_equal(got[out_off:out_off + b * h * w].view(np.uint32).reshape(b, h, w),
+                                  o.integral_image(img))
+    assert (got[:out_off] == 0x7FBADBAD).all() and (got[out_off + b * h * w:] == 0x7FBADBAD).all()
