@@ -764,7 +764,9 @@ def run_profile(args):
     the batched kernel on 1000 arrays of the batched length law (~1e8
     elements); `gridscan` a 2^26 int32 grid-scope scan; `reduce` a 2^26 fp32
     compensated tile reduce (W 32) then block reduce (B 256); `intimage` the
-    integral images of 64 8-bit 1080x1920 frames (three kernels)."""
+    integral images of 64 8-bit 1080x1920 frames (two kernels); `filter` the
+    aggregated filter of 2^26 keys at density 0.5; `coalesced` the group
+    size then the group shuffle over 2^26 half-active elements."""
     import torch
     from paper_2112_10034_gb300 import cox
     dev = torch.device("cuda", 0)
@@ -819,7 +821,24 @@ def run_profile(args):
         ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
         for _ in range(reps):
             chk(cox.cox_integral_image(3, B, H, W, img.data_ptr(), ii.data_ptr(), ws.data_ptr(), wsb, sh))
-        launches = reps * 3
+        launches = reps * 2
+    elif args.profile == "filter":
+        k = torch.from_numpy(inputs.uniform_u31(N_ELEMS, inputs.BASE_SEED + 2)).to(dev)
+        out = torch.empty(N_ELEMS, dtype=torch.int32, device=dev)
+        cnt = torch.empty(1, dtype=torch.int64, device=dev)
+        for _ in range(reps):
+            chk(cox.cox_filter_aggregated(0, k.data_ptr(), N_ELEMS, inputs.density_threshold(0.5), out.data_ptr(),
+                                          cnt.data_ptr(), sh))
+        launches = reps
+    elif args.profile == "coalesced":
+        g = torch.Generator(device="cpu").manual_seed(inputs.BASE_SEED + 4)
+        xa = torch.randint(-1000, 1001, (N_ELEMS,), generator=g, dtype=torch.int32).to(dev)
+        act = (torch.rand(N_ELEMS, generator=g) < 0.5).to(torch.int32).to(dev)
+        ya = torch.empty_like(xa)
+        for _ in range(reps):
+            for fn in (cox.COX_CG_SIZE, cox.COX_CG_SHFL):
+                chk(cox.cox_coalesced(fn, 0, 256, xa.data_ptr(), act.data_ptr(), ya.data_ptr(), N_ELEMS, 3, sh))
+        launches = reps * 2
     elif args.profile == "batch":
         lens = inputs.loguniform_lengths(1000, 32, 1 << 20, inputs.BASE_SEED + 3)
         vals = [torch.randn(int(L), device=dev) for L in lens]
@@ -847,7 +866,8 @@ def main():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--profile", choices=["scan", "compact", "hist", "batch", "gridscan", "reduce", "intimage"],
+    ap.add_argument("--profile", choices=["scan", "compact", "hist", "batch", "gridscan", "reduce", "intimage",
+                                          "filter", "coalesced"],
                     default=None,
                     help="small single-op case for ncu captures")
     args = ap.parse_args()
