@@ -6,8 +6,10 @@
 // of the SDK reduction kernels (Table 1): accumulator l starts at the
 // identity and folds partials l, l + 32, ..., and a width-32 tree over the
 // 32 accumulators gives the block's value.  Here the accumulators are
-// computed one per lane and the trees run level by level in shared memory,
-// their combines spread over the lanes (for 32-element blocks, each lane
+// computed one per lane (through shared memory when a block has more than
+// 32 tile partials) and the trees run as shuffles across the lanes; when a
+// block has at most 32 partials each accumulator holds one partial and the
+// tree runs within the block's own lanes (for 32-element blocks, each lane
 // owns a block and runs its tree in registers) -- the same combines in the
 // same order, so the same bits as the shuffle kernels.
 //
@@ -76,39 +78,57 @@ __device__ __forceinline__ void block_stage(typename R::V (&v)[32], void* smem, 
     return;
   }
   const int LB = 1024 / B, P = B / W;
+  if (P <= 32) {
+    // Accumulator l < P is (ident op partial l), the others stay identities,
+    // so the width-32 tree combines position i < P with an identity at every
+    // offset >= P, and at offsets below P with position i + off.  Position
+    // i = r * NT + j sits in slot j of the block's lane r (RB = B / 32 lanes
+    // per block): partners at offsets >= NT are lanes further down (a shuffle
+    // within the block for every position that is still read), partners at
+    // smaller offsets are slots of the same lane.  Same combines, same order.
+    const int RB = B / 32;
+    V a[NT];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) a[j] = R::op(R::ident(), v[j * W]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      if (off >= P) {
+#pragma unroll
+        for (int j = 0; j < NT; ++j) a[j] = R::op(a[j], R::ident());
+      } else if (off >= NT) {
+#pragma unroll
+        for (int j = 0; j < NT; ++j) a[j] = R::op(a[j], R::shfl_down(a[j], off / NT, 32));
+      } else {
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+          if (j < off) a[j] = R::op(a[j], a[j + off]);
+      }
+    }
+    const int64_t blk = lb0 + lane / RB;
+    if (lane % RB == 0 && blk < nvalid) {
+      out[blk] = to_bits(R::out(a[0]));
+      if (lo) lo[blk] = R::lo(a[0]);
+    }
+    return;
+  }
+  // More than 32 partials per block (P = 64 .. 512, so LB <= 8): the
+  // partials go through shared memory, lane l folds accumulator l of each
+  // block in order, and the width-32 tree runs across the lanes by shuffles.
   V* sp = reinterpret_cast<V*>(smem);
   __syncwarp();
 #pragma unroll
   for (int j = 0; j < NT; ++j) sp[part_slot(lane * NT + j)] = v[j * W];  // partial q = b * P + k
   __syncwarp();
-  V acc[16];
+#pragma unroll 1
+  for (int b = 0; b < LB; ++b) {
+    V acc = R::ident();
+    for (int k = lane; k < P; k += 32) acc = R::op(acc, sp[part_slot(b * P + k)]);
 #pragma unroll
-  for (int b = 0; b < 16; ++b) {
-    if (b < LB) {
-      acc[b] = R::ident();
-      for (int k = lane; k < P; k += 32) acc[b] = R::op(acc[b], sp[part_slot(b * P + k)]);
+    for (int off = 16; off > 0; off >>= 1) acc = R::op(acc, R::shfl_down(acc, off, 32));
+    if (lane == 0 && lb0 + b < nvalid) {
+      out[lb0 + b] = to_bits(R::out(acc));
+      if (lo) lo[lb0 + b] = R::lo(acc);
     }
-  }
-  __syncwarp();
-  // The width-32 trees of all LB blocks, level by level, spread over the
-  // lanes: at offset `off`, item w = b * off + i sets a(b, i) = a(b, i) op
-  // a(b, i + off); slots read at a level are never written at it.
-#pragma unroll
-  for (int b = 0; b < 16; ++b)
-    if (b < LB) sp[b * 32 + lane] = acc[b];
-  __syncwarp();
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    for (int w = lane; w < LB * off; w += 32) {
-      const int b = w / off, i = w % off;
-      sp[b * 32 + i] = R::op(sp[b * 32 + i], sp[b * 32 + i + off]);
-    }
-    __syncwarp();
-  }
-  if (lane < LB && lb0 + lane < nvalid) {
-    const V r = sp[lane * 32];
-    out[lb0 + lane] = to_bits(R::out(r));
-    if (lo) lo[lb0 + lane] = R::lo(r);
   }
   __syncwarp();
 }
