@@ -762,7 +762,8 @@ def run_profile(args):
     one 2^26-element input and one output; `compact` runs 2^26-key compactions
     at density 0.5; `hist` runs 2^26-key Zipf match histograms; `batch` runs
     the batched kernel on 1000 arrays of the batched length law (~1e8
-    elements); `gridscan` a 2^26 int32 grid-scope scan; `reduce` a 2^26 fp32
+    elements); `gridscan` a 2^26 int32 grid-scope scan (`gridscan_comp`: fp32
+    compensated); `reduce` a 2^26 fp32
     compensated tile reduce (W 32) then block reduce (B 256); `intimage` the
     integral images of 64 8-bit 1080x1920 frames (two kernels); `filter` the
     aggregated filter of 2^26 keys at density 0.5; `coalesced` the group
@@ -803,6 +804,15 @@ def run_profile(args):
         ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
         for _ in range(reps):
             chk(cox.cox_scan(0, 0, 2, 256, xi.data_ptr(), yi.data_ptr(), N_ELEMS, 0, 0, ws.data_ptr(), wsb, sh))
+        launches = reps
+    elif args.profile == "gridscan_comp":
+        xf = torch.from_numpy(inputs.normal_f32(N_ELEMS, inputs.BASE_SEED + 1)).to(dev)
+        yf = torch.empty_like(xf)
+        wsb = cox.cox_scan_workspace(2, N_ELEMS)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        for _ in range(reps):
+            chk(cox.cox_scan(0, 2, 2, 256, xf.data_ptr(), yf.data_ptr(), N_ELEMS, cox.COX_F_COMPENSATED, 0,
+                             ws.data_ptr(), wsb, sh))
         launches = reps
     elif args.profile == "reduce":
         x = torch.from_numpy(inputs.normal_f32(N_ELEMS, inputs.BASE_SEED + 1)).to(dev)
@@ -866,8 +876,8 @@ def main():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--profile", choices=["scan", "compact", "hist", "batch", "gridscan", "reduce", "intimage",
-                                          "filter", "coalesced"],
+    ap.add_argument("--profile", choices=["scan", "compact", "hist", "batch", "gridscan", "gridscan_comp", "reduce",
+                                          "intimage", "filter", "coalesced"],
                     default=None,
                     help="small single-op case for ncu captures")
     args = ap.parse_args()
