@@ -6,28 +6,16 @@
 // A warp's group is formed by a full-warp ballot of the activity flags; the
 // active lanes then run the warp intrinsics with that member mask
 // (shfl.sync / vote.sync / redux.sync with a partial mask), exactly as a
-// coalesced_group does.  Group ranks are popc(mask & lanemask_lt); the lane
-// of rank k is found by a 5-step binary search over popc prefixes, and the
-// group ballot is an OR-reduction of each member's vote shifted to its
-// rank.  The
+// coalesced_group does.  Group ranks are popc(mask & lanemask_lt); for the
+// shuffles, members write their lane into a per-warp rank -> lane table
+// and read the source rank's lane from it; the group ballot is an
+// OR-reduction of each member's vote shifted to its rank.  The
 // integer group scan alone runs over the full warp with inactive lanes
 // contributing 0 (the same sums, exactly).
 #include "cox_common.cuh"
 #include "compact_tile.cuh"
 
 namespace cox {
-
-// Lane of the k-th (0-based) set bit of mask; k < popc(mask).  (A 5-step
-// binary search over popc prefixes measured faster than __fns here.)
-__device__ __forceinline__ int nth_set_lane(unsigned mask, int k) {
-  int pos = 0;
-#pragma unroll
-  for (int b = 16; b > 0; b >>= 1) {
-    const int below = __popc(mask & ((1u << (pos + b)) - 1u));  // set bits below pos + b
-    if (below <= k) pos += b;
-  }
-  return pos;
-}
 
 template <int DT>
 __device__ __forceinline__ bool vote_pred(uint32_t u) {
@@ -36,17 +24,13 @@ __device__ __forceinline__ bool vote_pred(uint32_t u) {
 }
 
 // One group's function for one active lane (the lane's value v, the
-// group's mask, rank and size).  SCAN_SUM is handled by the caller.
+// group's mask, rank and size).  SCAN_SUM and the shuffles are handled by
+// the caller.
 template <int DT>
-__device__ __forceinline__ uint32_t group_fn(int fn, uint32_t v, unsigned mask, int rank, int size, int lane,
-                                             int param) {
+__device__ __forceinline__ uint32_t group_fn(int fn, uint32_t v, unsigned mask, int rank, int size) {
   switch (fn) {
     case COX_CG_SIZE: return (uint32_t)size;
     case COX_CG_RANK: return (uint32_t)rank;
-    case COX_CG_SHFL: return __shfl_sync(mask, v, nth_set_lane(mask, param % size));
-    case COX_CG_SHFL_UP: return __shfl_sync(mask, v, rank >= param ? nth_set_lane(mask, rank - param) : lane);
-    case COX_CG_SHFL_DOWN:
-      return __shfl_sync(mask, v, rank + param < size ? nth_set_lane(mask, rank + param) : lane);
     case COX_CG_BALLOT:  // bit k = the vote of rank k: each member ORs its vote in at its rank
       return __reduce_or_sync(mask, (vote_pred<DT>(v) ? 1u : 0u) << rank);
     case COX_CG_ANY: return __any_sync(mask, vote_pred<DT>(v)) ? 1u : 0u;
@@ -65,7 +49,8 @@ template <int DT>
 __global__ void __launch_bounds__(256) k_coalesced(int fn, const uint32_t* __restrict__ in,
                                                    const int32_t* __restrict__ active, uint32_t* __restrict__ out,
                                                    int64_t n, int param) {
-  const int lane = lane_id();
+  __shared__ uint8_t s_lane[8][32];  // per warp: lane of each group rank (shuffle functions)
+  const int lane = lane_id(), wib = threadIdx.x >> 5;
   const unsigned lt = lanemask_lt();
   const int64_t nw = (n + 32 * kCgUnroll - 1) / (32 * kCgUnroll);
   const int64_t wstep = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -92,8 +77,31 @@ __global__ void __launch_bounds__(256) k_coalesced(int fn, const uint32_t* __res
         if (act[u]) out[i] = x;
         continue;
       }
+      if (fn == COX_CG_SHFL || fn == COX_CG_SHFL_UP || fn == COX_CG_SHFL_DOWN) {
+        // rank -> lane table of this round's group: members write their lane
+        // at their rank, then read the source rank's lane
+        const int rank = __popc(mask & lt), size = __popc(mask);
+        if (act[u]) s_lane[wib][rank] = (uint8_t)lane;
+        __syncwarp();
+        if (act[u]) {
+          int want;
+          bool own = false;
+          if (fn == COX_CG_SHFL) {
+            want = param < size ? param : param % size;
+          } else if (fn == COX_CG_SHFL_UP) {
+            own = rank < param;
+            want = rank - param;
+          } else {
+            own = rank + param >= size;
+            want = rank + param;
+          }
+          out[i] = __shfl_sync(mask, v[u], own ? lane : (int)s_lane[wib][want]);
+        }
+        __syncwarp();  // the table's readers are done before the next round writes it
+        continue;
+      }
       if (!act[u]) continue;
-      out[i] = group_fn<DT>(fn, v[u], mask, __popc(mask & lt), __popc(mask), lane, param);
+      out[i] = group_fn<DT>(fn, v[u], mask, __popc(mask & lt), __popc(mask));
     }
   }
 }
