@@ -76,7 +76,8 @@ enum {
   COX_F_FP64_COMBINE = 2u, /* GRID scope fp32 sum: final cross-block combine in FP64 */
   COX_F_WS_READY = 4u,     /* compaction: caller zeroed the workspace; skip the memset */
   COX_F_NATIVE_MATCH = 8u, /* histograms: peer groups from the match.any.sync instruction */
-  COX_F_DIRECT_ATOMICS = 16u /* histograms: no peer groups, one shared atomic per key */
+  COX_F_DIRECT_ATOMICS = 16u, /* histograms: no peer groups, one shared atomic per key */
+  COX_F_BALLOT_MATCH = 32u    /* histograms: peer groups from ballots over the key bits */
 };
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -352,10 +353,14 @@ cox_status cox_ballot_compact_static(cox_dtype dt, int width, int block_dim, con
  * Per tile: peers = match_any(key) among the lanes whose key is in [0, bins);
  * the lowest lane of each peer group adds popc(peers) to a shared-memory bin;
  * blocks merge into d_hist.  Same family of warp functions as Section 2.2.1.
- * By default the peer mask comes from ceil(log2(bins)) + 1 ballots (lanes
- * agree on a key iff they agree on every key bit), which is exactly the mask
- * __match_any_sync returns; COX_F_NATIVE_MATCH takes it from the
- * match.any.sync instruction instead (same result, slower on sm_103a).
+ * By default the peer mask comes from a per-warp table in shared memory
+ * (each in-range lane ORs its lane bit into its key's word, then reads the
+ * word back: the lanes holding that key) when two tables of `bins` words
+ * per warp fit next to the histograms, else from ceil(log2(bins)) + 1
+ * ballots (lanes agree on a key iff they agree on every key bit); both are
+ * exactly the mask __match_any_sync returns.  COX_F_BALLOT_MATCH forces the
+ * ballots; COX_F_NATIVE_MATCH takes the mask from the match.any.sync
+ * instruction instead (same result, slower on sm_103a).
  * COX_F_DIRECT_ATOMICS skips the peer groups: every key adds one to its
  * shared bin (same counts; on sm_103a shared atomics absorb Zipf-skewed keys
  * at memory speed, so this is the fastest histogram, but it is not built
@@ -364,7 +369,8 @@ cox_status cox_ballot_compact_static(cox_dtype dt, int width, int block_dim, con
  *   d_hist: `bins` int32 counters, overwritten (zeroed by the call).
  *   d_ignored: optional int64 (may be NULL): number of keys outside [0, bins),
  *   overwritten.
- *   flags: 0, COX_F_NATIVE_MATCH or COX_F_DIRECT_ATOMICS.
+ *   flags: 0 or one of COX_F_NATIVE_MATCH, COX_F_BALLOT_MATCH,
+ *   COX_F_DIRECT_ATOMICS.
  */
 cox_status cox_match_histogram(cox_dtype dt, int width, int block_dim, const void* d_keys, int64_t n,
                                int bins, int32_t* d_hist, int64_t* d_ignored, unsigned flags, void* stream);
@@ -375,7 +381,7 @@ cox_status cox_match_histogram(cox_dtype dt, int width, int block_dim, const voi
 /* ====================================================================== */
 
 /* Launch shape of the batched kernel.  Every field must be set (or pass a
- * NULL tune to take the library default, {512, 2, 32, 8, 0}). */
+ * NULL tune to take the library default, {512, 2, 32, 8, 3}). */
 typedef struct {
   int block_dim;     /* threads per CTA, multiple of 32 in [64, 1024] */
   int ctas_per_sm;   /* persistent CTAs per SM, 1..8 */
@@ -383,7 +389,9 @@ typedef struct {
   int fp64_segments; /* arrays split over >= this many CTAs combine in FP64 (>= 1) */
   int native_match;  /* peer groups of the histogram step: 0 the match_any masks from 9 ballots,
                         1 the match.any.sync instruction, 2 none (one shared atomic per key;
-                        same counts, not built from match_any) */
+                        same counts, not built from match_any), 3 the match_any masks from a
+                        per-warp table in shared memory (lanes OR their bit into their key's
+                        word and read it back) */
 } cox_batch_tune;
 
 /* Bytes of device workspace for a batch of num_arrays arrays (any tune). */

@@ -25,7 +25,8 @@ COX_SCOPE_TILE, COX_SCOPE_BLOCK, COX_SCOPE_GRID = 0, 1, 2
 COX_GRID_SUB_MIN, COX_GRID_NORMALIZE = 0, 1
 (COX_CG_SIZE, COX_CG_RANK, COX_CG_SHFL, COX_CG_SHFL_UP, COX_CG_SHFL_DOWN, COX_CG_BALLOT, COX_CG_ANY, COX_CG_ALL,
  COX_CG_REDUCE_SUM, COX_CG_SCAN_SUM) = range(10)
-COX_F_COMPENSATED, COX_F_FP64_COMBINE, COX_F_WS_READY, COX_F_NATIVE_MATCH, COX_F_DIRECT_ATOMICS = 1, 2, 4, 8, 16
+(COX_F_COMPENSATED, COX_F_FP64_COMBINE, COX_F_WS_READY, COX_F_NATIVE_MATCH, COX_F_DIRECT_ATOMICS,
+ COX_F_BALLOT_MATCH) = 1, 2, 4, 8, 16, 32
 FULL_MASK = 0xFFFFFFFF
 
 _P = ctypes.c_void_p
@@ -378,7 +379,7 @@ def ballot_compact(keys, threshold: int, width: int = 32, block_dim: int = 256, 
 
 
 def match_histogram(keys, bins: int = 256, width: int = 32, block_dim: int = 256, unsigned: bool = False,
-                    native_match: bool = False, direct: bool = False):
+                    native_match: bool = False, direct: bool = False, ballot_match: bool = False):
     """Match-any histogram (cox_match_histogram).  Returns (hist int32[bins], ignored int64[1])."""
     t = _torch()
     keys = _dev_tensor(keys)
@@ -386,8 +387,9 @@ def match_histogram(keys, bins: int = 256, width: int = 32, block_dim: int = 256
     ign = t.empty(1, dtype=t.int64, device=keys.device)
     _check(cox_match_histogram(COX_U32 if unsigned else COX_I32, width, block_dim, keys.data_ptr(), keys.numel(),
                                bins, hist.data_ptr(), ign.data_ptr(),
-                               (COX_F_NATIVE_MATCH if native_match else 0) | (COX_F_DIRECT_ATOMICS if direct else 0),
-                               _stream(keys.device)), "cox_match_histogram")
+                               (COX_F_NATIVE_MATCH if native_match else 0) | (COX_F_DIRECT_ATOMICS if direct else 0)
+                               | (COX_F_BALLOT_MATCH if ballot_match else 0), _stream(keys.device)),
+           "cox_match_histogram")
     return hist, ign
 
 

@@ -1,5 +1,6 @@
 // Batched uneven arrays: per array a compensated fp32 sum and a 256-bin
-// histogram built with __match_any_sync, all arrays in one persistent launch.
+// histogram built from match_any peer groups, all arrays in one persistent
+// launch.
 //
 // Work split.  The arrays are laid end to end in a virtual index space of E
 // elements (prefix sums of the lengths, written once by cox_batch_prepare).
@@ -28,7 +29,7 @@ namespace cox {
 constexpr int kBatchBins = 256;
 constexpr int kBatchMaxCtas = 4096;
 constexpr size_t kBatchHeader = 256;
-constexpr cox_batch_tune kDefaultTune = {512, 2, 32, 8, 0};
+constexpr cox_batch_tune kDefaultTune = {512, 2, 32, 8, 3};
 
 __host__ __device__ __forceinline__ int64_t cta_begin(int64_t i, int64_t E, int64_t G) {
   return (int64_t)(((uint64_t)i * (uint64_t)E) / (uint64_t)G);
@@ -42,23 +43,38 @@ __device__ __forceinline__ int64_t cta_of(int64_t pos, int64_t E, int64_t G) {
 
 // Histogram step of one warp: peers among the lane's width-W tile with the
 // same in-range key; the lowest peer adds the group's size to the warp's bins.
-// The peer mask comes from 9 ballots over the key bits, or (NATIVE) from the
-// match.any.sync instruction: the same mask either way.
-// PEER: 0 ballots over the key bits, 1 the match.any.sync instruction, 2 no
-// peer groups (one shared atomic per key; same counts).
+// PEER: 0 the match_any mask from 9 ballots over the key bits, 1 the
+// match.any.sync instruction, 3 a per-warp table in shared memory (each
+// in-range lane ORs its lane bit into its key's word and reads the word back;
+// two tables used in turn, each word cleared by its key's lowest lane after
+// every lane has read it) -- the same mask every way; 2 no peer groups (one
+// shared atomic per key; same counts).
 template <int W, int PEER>
-__device__ __forceinline__ void batch_hist_step(uint32_t key, bool valid, uint32_t* my) {
+__device__ __forceinline__ void batch_hist_step(uint32_t key, bool valid, uint32_t* my, uint32_t* tab, int& tsel) {
   const int lane = lane_id();
   const bool in = valid && key < (uint32_t)kBatchBins;
   if constexpr (PEER == 2) {
     if (in) atomicAdd(my + key, 1u);
   } else {
     const unsigned tmask = W == 32 ? kFull : (((1u << W) - 1u) << (lane & ~(W - 1)));
+    const unsigned lt = lanemask_lt();
     unsigned peers;
-    if constexpr (PEER == 1) peers = __match_any_sync(kFull, key) & __ballot_sync(kFull, in);
-    else peers = match_any_bits<8>(key, in);
+    if constexpr (PEER == 3) {
+      uint32_t* t = tab + tsel * kBatchBins;
+      tsel ^= 1;
+      if (in) atomicOr(t + key, 1u << lane);
+      __syncwarp();
+      const unsigned all = in ? t[key] : 0u;
+      __syncwarp();
+      if (in && (all & lt) == 0u) t[key] = 0u;
+      peers = all;
+    } else if constexpr (PEER == 1) {
+      peers = __match_any_sync(kFull, key) & __ballot_sync(kFull, in);
+    } else {
+      peers = match_any_bits<8>(key, in);
+    }
     peers &= tmask;
-    if (in && (peers & lanemask_lt()) == 0u) atomicAdd(my + key, (uint32_t)__popc(peers));
+    if (in && (peers & lt) == 0u) atomicAdd(my + key, (uint32_t)__popc(peers));
   }
 }
 
@@ -69,7 +85,7 @@ __device__ __forceinline__ void fold(Pair& acc, float x) { acc = Comp::op(acc, C
 // part with valid = false).
 template <int W, int PEER>
 __device__ void batch_segment(const float* __restrict__ v, const int32_t* __restrict__ k, int64_t s0, int64_t s1,
-                              Pair& acc, uint32_t* my) {
+                              Pair& acc, uint32_t* my, uint32_t* tab, int& tsel) {
   const int lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uintptr_t pv = reinterpret_cast<uintptr_t>(v), pk = reinterpret_cast<uintptr_t>(k);
   // 128-bit loads need values and keys at the same phase modulo 16 bytes
@@ -81,7 +97,7 @@ __device__ void batch_segment(const float* __restrict__ v, const int32_t* __rest
       const float x = ok ? __ldcs(v + e) : 0.0f;
       const uint32_t key = ok ? (uint32_t)__ldcs(k + e) : 0u;
       if (ok) fold(acc, x);
-      batch_hist_step<W, PEER>(key, ok, my);
+      batch_hist_step<W, PEER>(key, ok, my, tab, tsel);
     }
     return;
   }
@@ -96,7 +112,7 @@ __device__ void batch_segment(const float* __restrict__ v, const int32_t* __rest
     const float x = ok ? __ldcs(v + e) : 0.0f;
     const uint32_t key = ok ? (uint32_t)__ldcs(k + e) : 0u;
     if (ok) fold(acc, x);
-    batch_hist_step<W, PEER>(key, ok, my);
+    batch_hist_step<W, PEER>(key, ok, my, tab, tsel);
   }
   // body: warp steps of 128 elements (one 128-bit load of values and of keys
   // per lane), two steps in flight
@@ -127,7 +143,7 @@ __device__ void batch_segment(const float* __restrict__ v, const int32_t* __rest
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       if (ok[j]) fold(acc, x[j]);
-      batch_hist_step<W, PEER>(key[j], ok[j], my);
+      batch_hist_step<W, PEER>(key[j], ok[j], my, tab, tsel);
     }
   }
 }
@@ -137,11 +153,14 @@ __global__ void __launch_bounds__(1024) k_batch_sum_hist(const float* const* __r
                                                          const int32_t* const* __restrict__ keys,
                                                          const int64_t* __restrict__ off, int64_t A,
                                                          float2* __restrict__ part, int32_t* __restrict__ hists) {
-  extern __shared__ uint32_t sh[];  // (blockDim / 32) x 256 per-warp bins
+  extern __shared__ uint32_t sh[];  // (blockDim / 32) x 256 per-warp bins, then the peer tables
   __shared__ Pair wpart[32];
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < nw * kBatchBins; i += blockDim.x) sh[i] = 0u;
+  const int ntab = PEER == 3 ? nw * 2 * kBatchBins : 0;
+  for (int i = threadIdx.x; i < nw * kBatchBins + ntab; i += blockDim.x) sh[i] = 0u;
   __syncthreads();
+  uint32_t* tab = sh + nw * kBatchBins + warp * 2 * kBatchBins;
+  int tsel = 0;
   const int64_t E = off[A];
   const int64_t G = gridDim.x;
   const int64_t lo = cta_begin(blockIdx.x, E, G), hi = cta_begin(blockIdx.x + 1, E, G);
@@ -160,7 +179,7 @@ __global__ void __launch_bounds__(1024) k_batch_sum_hist(const float* const* __r
     const int64_t base = off[a];
     const int64_t end = min(hi, off[a + 1]);
     Pair acc = Comp::ident();
-    batch_segment<W, PEER>(vals[a], keys[a], pos - base, end - base, acc, my);
+    batch_segment<W, PEER>(vals[a], keys[a], pos - base, end - base, acc, my, tab, tsel);
     const Pair s = block_reduce32<Comp>(acc, wpart);  // ends with __syncthreads
     if (threadIdx.x == 0) part[a + blockIdx.x] = make_float2(s.s, s.e);
     for (int b = threadIdx.x; b < kBatchBins; b += blockDim.x) {
@@ -213,7 +232,7 @@ __global__ void k_batch_combine(const int64_t* __restrict__ off, int64_t A, int 
 bool tune_ok(const cox_batch_tune& t) {
   return t.block_dim >= 64 && t.block_dim <= 1024 && t.block_dim % 32 == 0 && t.ctas_per_sm >= 1 &&
          t.ctas_per_sm <= 8 && valid_width(t.width) && t.fp64_segments >= 1 &&
-         (t.native_match >= 0 && t.native_match <= 2);
+         (t.native_match >= 0 && t.native_match <= 3);
 }
 
 struct BatchWs {
@@ -272,10 +291,20 @@ extern "C" cox_status cox_batch_sum_hist(int64_t num_arrays, const float* const*
   if (G > kBatchMaxCtas) G = kBatchMaxCtas;
   if (cudaMemsetAsync(d_hists, 0, (size_t)num_arrays * kBatchBins * sizeof(int32_t), st) != cudaSuccess)
     return COX_ECUDA;
-  const size_t smem = (size_t)(t.block_dim / 32) * kBatchBins * sizeof(uint32_t);
+  const size_t smem = (size_t)(t.block_dim / 32) * kBatchBins * sizeof(uint32_t) *
+                      (t.native_match == 3 ? 3 : 1);  // per-warp bins (+ two peer tables)
   const cox_status s = with_width(t.width, [&](auto wc) {
     constexpr int W = decltype(wc)::value;
-    if (t.native_match == 1)
+    if (t.native_match == 3) {
+      auto k = k_batch_sum_hist<W, 3>;
+      static bool attr = false;  // up to 96 KB of shared memory
+      if (!attr) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024) != cudaSuccess)
+          return COX_ECUDA;
+        attr = true;
+      }
+      k<<<G, t.block_dim, smem, st>>>(d_vals, d_keys, w.off, num_arrays, w.part, d_hists);
+    } else if (t.native_match == 1)
       k_batch_sum_hist<W, 1><<<G, t.block_dim, smem, st>>>(d_vals, d_keys, w.off, num_arrays, w.part, d_hists);
     else if (t.native_match == 2)
       k_batch_sum_hist<W, 2><<<G, t.block_dim, smem, st>>>(d_vals, d_keys, w.off, num_arrays, w.part, d_hists);
@@ -391,7 +420,7 @@ extern "C" cox_status cox_batch_autotune(int64_t num_arrays, const float* const*
     for (int c : cpsm)
       for (int wdt : widths) {
         if (b * c > 2048) continue;  // more threads than an SM holds
-        const cox_batch_tune t = {b, c, wdt, kDefaultTune.fp64_segments, 0};
+        const cox_batch_tune t = {b, c, wdt, kDefaultTune.fp64_segments, kDefaultTune.native_match};
         rc = cox_batch_sum_hist(num_arrays, d_vals, d_keys, &t, d_workspace, workspace_bytes, d_sums, nullptr,
                                 d_hists, stream);  // warm-up
         if (rc != COX_OK) goto done;

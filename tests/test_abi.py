@@ -93,5 +93,6 @@ def test_host_validation(cox):
     # histogram bins range
     assert cox.cox_match_histogram(0, 32, 256, 16, 10, 0, 16, None, 0, None) == E
     assert cox.cox_match_histogram(0, 32, 256, 16, 10, 8193, 16, None, 0, None) == E
-    assert cox.cox_match_histogram(0, 32, 256, 16, 10, 256, 16, None, 32, None) == E
+    assert cox.cox_match_histogram(0, 32, 256, 16, 10, 256, 16, None, 64, None) == E
+    assert cox.cox_match_histogram(0, 32, 256, 16, 10, 256, 16, None, 8 | 32, None) == E
     assert cox.cox_match_histogram(0, 32, 256, 16, 10, 256, 16, None, 8 | 16, None) == E

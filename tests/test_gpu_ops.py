@@ -401,11 +401,22 @@ def test_histogram_is_bit_exact(cox, W, bins):
         z[::13] = -1
         z[5::17] = bins + 3
         want, wign = o.match_histogram(W, B, z, bins)
-        for native, direct in ((False, False), (True, False), (False, True)):
+        for native, direct, ballot in ((False, False, False), (True, False, False), (False, True, False),
+                                       (False, False, True)):
             hist, ign = cox.match_histogram(dev(z), bins=bins, width=W, block_dim=B, native_match=native,
-                                            direct=direct)
+                                            direct=direct, ballot_match=ballot)
             np.testing.assert_array_equal(host(hist), want)
             assert int(ign.item()) == wign
+
+
+def test_histogram_flags(cox):
+    import torch
+    z = torch.zeros(64, dtype=torch.int32, device="cuda")
+    h = torch.zeros(256, dtype=torch.int32, device="cuda")
+    for bad in (cox.COX_F_NATIVE_MATCH | cox.COX_F_BALLOT_MATCH, cox.COX_F_DIRECT_ATOMICS | cox.COX_F_BALLOT_MATCH,
+                cox.COX_F_COMPENSATED):
+        assert cox.cox_match_histogram(0, 32, 256, z.data_ptr(), 64, 256, h.data_ptr(), None, bad,
+                                       None) == cox.COX_EINVAL
 
 
 # ------------------------------------------------------------ full sizes
