@@ -11,7 +11,8 @@
 // of shared memory each) are read once: each CTA's slice arrives by TMA bulk
 // copies, is reduced from shared memory, kept there across the barrier,
 // transformed in place and written back by TMA bulk stores.  Larger arrays
-// are streamed twice (grid-stride loops before and after the barrier).
+// are streamed twice (grid-stride loops before and after the barrier, the
+// second one backwards so that it starts on the lines still in L2).
 #include "cox_common.cuh"
 
 namespace cox {
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(kGbThreads) k_grid_bcast(const uint32_t* in, u
     const int64_t gt = (int64_t)blockIdx.x * kGbThreads + tid, gs = (int64_t)gridDim.x * kGbThreads;
     const uint4* p = reinterpret_cast<const uint4*>(in);
     for (int64_t i = gt; i < n / 4; i += gs) {
-      const uint4 q = __ldcs(p + i);
+      const uint4 q = __ldcg(p + i);  // kept in L2: phase 2 re-reads the last of it from there
       acc.add(q.x);
       acc.add(q.y);
       acc.add(q.z);
@@ -226,7 +227,10 @@ __global__ void __launch_bounds__(kGbThreads) k_grid_bcast(const uint32_t* in, u
     const int64_t gt = (int64_t)blockIdx.x * kGbThreads + tid, gs = (int64_t)gridDim.x * kGbThreads;
     const uint4* p = reinterpret_cast<const uint4*>(in);
     uint4* q = reinterpret_cast<uint4*>(out);
-    for (int64_t i = gt; i < n / 4; i += gs) {
+    // backwards: phase 1 ended on the array's tail, whose lines are still in
+    // L2, so those are read first (output stores stream past L2)
+    for (int64_t j = gt; j < n / 4; j += gs) {
+      const int64_t i = n / 4 - 1 - j;
       uint4 v = __ldcs(p + i);
       v.x = apply<OP, DT>(v.x, mbits, norm);
       v.y = apply<OP, DT>(v.y, mbits, norm);
