@@ -412,8 +412,8 @@ def run_secondary(dev, st):
     ms = _time_launches(st, lambda: chk(cox.cox_match_histogram(0, 32, 256, z.data_ptr(), n, 256, hist.data_ptr(),
                                                                 None, 0, sh)))
     gbs = n * 4 / (ms * 1e-3) / 1e9
-    hres = {"ballot_peer_masks": {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3)}}
-    for name, fl in (("native_match_any", 8), ("direct_atomics_no_match", 16)):
+    hres = {"table_peer_masks": {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3)}}
+    for name, fl in (("ballot_peer_masks", 32), ("native_match_any", 8), ("direct_atomics_no_match", 16)):
         ms = _time_launches(st, lambda: chk(cox.cox_match_histogram(0, 32, 256, z.data_ptr(), n, 256, hist.data_ptr(),
                                                                     None, fl, sh)))
         gbs = n * 4 / (ms * 1e-3) / 1e9
