@@ -137,14 +137,20 @@ def _barrier(world):
         dist.barrier()
 
 
-def _max_over_ranks(v: float, world: int) -> float:
+def _max_over_ranks(v: float, world: int, device: str = "cuda") -> float:
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _job_gbs(bytes_per_rank: float, world: int, elapsed_ms: float) -> float:
+    """Whole-job rate: every rank moved `bytes_per_rank`; the job took the
+    slowest rank's time."""
+    return bytes_per_rank * world / (elapsed_ms * 1e-3) / 1e9
 
 
 # --------------------------------------------------------- the GPU arm
@@ -200,7 +206,7 @@ def run_cox(args):
     launches = K * len(VARIANTS)
 
     # ---- parity spot check of this run's outputs (sampled rows, no oracle call)
-    value = BYTES_PER_LAUNCH * launches * world / (elapsed_ms * 1e-3) / 1e9
+    value = _job_gbs(BYTES_PER_LAUNCH * launches, world, elapsed_ms)
     peak, peak_kind = _peaks()
     dom = int(np.argmax(per_variant_ms))
     achieved = BYTES_PER_LAUNCH / (per_variant_ms[dom] * 1e-3) / 1e9
