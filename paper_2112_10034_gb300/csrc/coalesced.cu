@@ -112,16 +112,18 @@ __global__ void __launch_bounds__(256) k_coalesced(int fn, const uint32_t* __res
 // slot is the warp's base + that offset + its rank.  The warps of a CTA
 // aggregate once more: one atomic per CTA per chunk of 8 x 512 keys
 // reserves the warps' totals, and warp w's base follows warps 0 .. w-1.
-// Chunks (16 KB) reach shared memory by TMA bulk copies, two ahead of the
-// one being processed.
+// Chunks (16 KB) reach shared memory by TMA bulk copies, one ahead of the
+// one being processed: two slots keep the kernel at 40 registers and 32 KB
+// of shared memory, so six CTAs fit per SM -- more warps to issue from,
+// which this issue-bound kernel needs more than a deeper pipeline.
 constexpr int kFilterRounds = 16;
 constexpr int kFilterWarps = 8;
-constexpr int kFilterStages = 3;
+constexpr int kFilterStages = 2;
 constexpr int kFilterChunk = 32 * kFilterRounds * kFilterWarps;  // keys per CTA iteration
 constexpr size_t kFilterSmem = (size_t)kFilterStages * kFilterChunk * sizeof(uint32_t);
 
 template <bool SIGNED>
-__global__ void __launch_bounds__(32 * kFilterWarps, 4)
+__global__ void __launch_bounds__(32 * kFilterWarps, 5)
     k_filter_aggregated(const uint32_t* __restrict__ keys, int64_t n, KeepRule rule, uint32_t* __restrict__ out,
                         unsigned long long* __restrict__ count, uint32_t limit, unsigned* status, int vec) {
   extern __shared__ __align__(16) uint32_t fbuf[];
