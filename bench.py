@@ -44,7 +44,7 @@ WORKLOAD = ("tile inclusive scan (shfl_up, cg tiles) of 2^26 fp32 N(0,1) at widt
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture, valid
 # only while the kernel sources hash to `src_sha` (else reported as null).
-NCU_TRAFFIC = {"src_sha": "a341b3836c261551",  # profiles/tile_scan_2p26_fp32_ncu.md
+NCU_TRAFFIC = {"src_sha": "a341b3836c261551",
                "bytes_per_launch": {
                                     "k_tile_scan_rows<Plain<AddF>, 16>": 268460544 + 216219648,
                                     "k_tile_scan_rows<Comp, 16>": 268481024 + 217029632,
@@ -205,7 +205,6 @@ def run_cox(args):
                       for i in range(len(VARIANTS))]
     launches = K * len(VARIANTS)
 
-    # ---- parity spot check of this run's outputs (sampled rows, no oracle call)
     value = _job_gbs(BYTES_PER_LAUNCH * launches, world, elapsed_ms)
     peak, peak_kind = _peaks()
     dom = int(np.argmax(per_variant_ms))
@@ -248,6 +247,7 @@ def run_cox(args):
         result["secondary"] = run_secondary(dev, st)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         result["cpu_baseline"] = cpu_baseline(target_s=args.cpu_seconds)
+        result["precision"] = oracle_precision(x_host, outs)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -722,6 +722,41 @@ def cpu_baseline(target_s: float = 12.0):
     gbs = n * 8 * len(VARIANTS) * passes / total / 1e9
     return {"value": round(gbs, 4), "unit": "GB/s", "cores": o.threads(), "kind": "oracle",
             "sample": f"first {n} of the 2^26 elements, all 8 width/mode scans, {passes} passes, {total:.1f} s"}
+
+
+def _err_stats(y, ref, ab):
+    """Errors of fp32 results y against FP64 values ref (sum|x| of the inputs
+    of each output in ab): the tolerance metric |y - r| / max(|r|, 2^-24
+    sum|x|) (max), pointwise |y - r| / |r| over r != 0 (max and p99), and the
+    normwise ||y - r||_2 / ||r||_2."""
+    y = y.astype(np.float64)
+    d = np.abs(y - ref)
+    den = np.maximum(np.abs(ref), 2.0 ** -24 * ab)
+    tol_metric = float(np.max(d / np.where(den == 0, 1.0, den)))
+    nz = ref != 0
+    pw = d[nz] / np.abs(ref[nz])
+    return {"max": tol_metric, "pointwise_max": float(pw.max()), "pointwise_p99": float(np.percentile(pw, 99)),
+            "normwise": float(np.linalg.norm(y - ref) / np.linalg.norm(ref))}
+
+
+def oracle_precision(x_host, outs):
+    """Part of the oracle leg (outside every timed region): the error of each
+    of the 8 timed scans' outputs, as they stand after the last timed step,
+    against the oracle's FP64 tile prefix of the same 2^26 inputs."""
+    import oracle as o
+    rows, refs = {}, {}
+    for (w, comp), out in zip(VARIANTS, outs):
+        if w not in refs:
+            _, ref, ab = o.scan_ref(o.SUM, o.F32, w, x_host)
+            refs = {w: (ref, ab)}
+        ref, ab = refs[w]
+        e = _err_stats(out.cpu().numpy(), ref, ab)
+        rows[f"W{w}_{'comp' if comp else 'plain'}"] = {k: float(f"{v:.3e}") for k, v in e.items()}
+        rows[f"W{w}_{'comp' if comp else 'plain'}"]["meets_1e-5"] = e["max"] <= 1e-5
+    return {"reference": "oracle FP64 tile prefix (Neumaier) of the same 2^26 fp32 inputs",
+            "metric": "max = max |y-r|/max(|r|, 2^-24 sum|x|) (the 1e-5 bar, gated for compensated); "
+                      "pointwise over r != 0; normwise ||y-r||_2/||r||_2",
+            "rows": rows}
 
 
 def run_reference(args):

@@ -339,9 +339,14 @@ size_t cox_ballot_compact_workspace(int64_t n, int block_dim);
  * bytes it uses with a cudaMemsetAsync on `stream` before its kernel.
  * The first call on a device looks up the array's device address (with that
  * device current) and caches it; make that first call before any stream
- * capture on the device.  All calls share the one array: calls whose work
- * overlaps on the GPU (other streams, other threads) race on it and must be
- * serialised by the caller.
+ * capture on the device.  Under CUDA's lazy module loading that lookup may be
+ * what loads the library's device code on that device, which takes device
+ * memory and synchronises; if that load fails the call returns COX_ECUDA.
+ * The cached address belongs to the device's primary context: after
+ * cudaDeviceReset on that device, do not call this entry point again in the
+ * same process.  All calls share the one array: calls whose work overlaps on
+ * the GPU (other streams, other threads) race on it and must be serialised
+ * by the caller.
  */
 #define COX_COMPACT_STATIC_SCRATCH_BYTES (1u << 20)
 cox_status cox_ballot_compact_static(cox_dtype dt, int width, int block_dim, const void* d_keys, int64_t n,

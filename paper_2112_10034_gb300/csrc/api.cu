@@ -9,7 +9,7 @@ namespace {
 
 __device__ unsigned g_dev_status;  // bit flags (cox::kDevTimeout)
 
-constexpr int kMaxDevices = 64;
+using cox::kMaxDevices;
 unsigned* g_status_addr[kMaxDevices];
 int g_sms[kMaxDevices];
 std::mutex g_mu;
@@ -40,6 +40,8 @@ unsigned* device_status_word() {
 }
 
 uint32_t spin_limit() { return g_spin_limit; }
+
+int device_index() { return current_device(); }
 
 int sm_count() {
   const int d = current_device();

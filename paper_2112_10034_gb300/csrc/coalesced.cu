@@ -123,7 +123,7 @@ constexpr int kFilterChunk = 32 * kFilterRounds * kFilterWarps;  // keys per CTA
 constexpr size_t kFilterSmem = (size_t)kFilterStages * kFilterChunk * sizeof(uint32_t);
 
 template <bool SIGNED>
-__global__ void __launch_bounds__(32 * kFilterWarps, 5)
+__global__ void __launch_bounds__(32 * kFilterWarps, 6)
     k_filter_aggregated(const uint32_t* __restrict__ keys, int64_t n, KeepRule rule, uint32_t* __restrict__ out,
                         unsigned long long* __restrict__ count, uint32_t limit, unsigned* status, int vec) {
   extern __shared__ __align__(16) uint32_t fbuf[];
@@ -214,7 +214,8 @@ template <int DT>
 static cox_status launch_coalesced(int fn, const void* d_in, const int32_t* d_active, void* d_out, int64_t n,
                                    int param, cudaStream_t st) {
   auto k = k_coalesced<DT>;
-  static int g = 0;  // persistent grid of this instance
+  static int grid[kMaxDevices];  // persistent grid of this instance, per device
+  int& g = grid[device_index()];
   if (g == 0) g = persistent_grid(k, 256, 0, 1 << 30);
   const int64_t ctas = ((n + 32 * kCgUnroll - 1) / (32 * kCgUnroll) + 7) / 8;
   k<<<(int)(ctas < g ? ctas : g), 256, 0, st>>>(fn, static_cast<const uint32_t*>(d_in), d_active,
@@ -226,7 +227,8 @@ template <bool SIGNED>
 static cox_status launch_filter(const void* d_keys, int64_t n, int64_t threshold, void* d_out, int64_t* d_count,
                                 cudaStream_t st) {
   auto k = k_filter_aggregated<SIGNED>;
-  static int g = 0;
+  static int grid[kMaxDevices];  // per device: the attribute and the occupancy are per-device state
+  int& g = grid[device_index()];
   if (g == 0) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFilterSmem) != cudaSuccess)
       return COX_ECUDA;

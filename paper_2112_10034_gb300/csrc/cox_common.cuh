@@ -607,6 +607,8 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 int sm_count();  // of the current device (cached per device)
+constexpr int kMaxDevices = 64;  // per-device caches hold this many ordinals
+int device_index();  // the current device's ordinal, clamped into [0, kMaxDevices)
 
 inline cox_status launch_status() {
   return cudaGetLastError() == cudaSuccess ? COX_OK : COX_ECUDA;

@@ -1,17 +1,22 @@
 """GPU parity: every op through the C ABI against the CPU oracle.
 
 Integer, vote, match, compaction and histogram results must be bit-exact.
-fp32 TILE/BLOCK reductions and tile scans follow the oracle's association
-order exactly, so they must be bit-exact against its fp32 emulation too;
-every fp32 sum must also meet |y - r| / max(|r|, 2^-24 sum|x|) <= 1e-5
-against the FP64 definition when compensated.  Outputs are poisoned first so
-that writes past the valid range are caught.
+Every fp32 sum and scan is checked against the FP64 definition (the
+oracle's reference value r and sum|x| of the same inputs): compensated
+results to |y - r| / max(|r|, 2^-24 sum|x|) <= 1e-5 at every output, plain
+ones to the tree-depth bound gamma_h sum|x| of the order the kernel states
+(tests/fpcheck.py); fp32 min/max are exact.  fp32 TILE/BLOCK reductions and
+tile scans follow the oracle's association order exactly, so they must also
+be bit-exact against its fp32 emulation -- a second layer on top of the
+definition.  Outputs are poisoned first so that writes past the valid range
+are caught.
 """
 import numpy as np
 import pytest
 
 import oracle as o
 from paper_2112_10034_gb300 import inputs
+from tests import fpcheck as fc
 
 pytestmark = pytest.mark.gpu
 
@@ -54,6 +59,25 @@ def _data(dt, n, seed):
     if dt == o.F32:
         return inputs.normal_f32(n, seed)
     return inputs.bits_u32(n, seed).view(_np_dtype(dt))
+
+
+def _check_reduce_def(got, op, dt, W, B, scope, x, comp=False, what=""):
+    """TILE/BLOCK reduction results against the plain definition."""
+    seg = W if scope == o.TILE else B
+    bits, ref, ab = o.reduce_ref(op, dt, seg, x)
+    if dt == o.F32 and op == o.SUM:
+        depth = fc.tile_depth(W) if scope == o.TILE else fc.block_depth(W, B)
+        fc.assert_fp64(got.view(np.float32), ref, ab, comp, depth, what)
+    else:
+        np.testing.assert_array_equal(got.view(np.uint32), bits.view(np.uint32), err_msg=what)
+
+
+def _check_scan_def(got, op, dt, W, x, comp=False, what=""):
+    """Tile-scan results against the plain definition."""
+    bits, ref, ab = o.scan_ref(op, dt, W, x)
+    if dt == o.F32 and op == o.SUM:
+        return fc.assert_fp64(got.view(np.float32), ref, ab, comp, fc.tile_depth(W), what)
+    np.testing.assert_array_equal(got.view(np.uint32), bits.view(np.uint32), err_msg=what)
 
 
 def _torch_view(t, dt):
@@ -145,6 +169,7 @@ def test_tile_and_block_reduce_match_the_emulation(cox, dt, op, W):
             want, _ = o.reduce_emulate(op, dt, W, B, scope, x)
             np.testing.assert_array_equal(got[:m].view(np.uint32), want.view(np.uint32),
                                           err_msg=f"n={n} B={B} scope={scope}")
+            _check_reduce_def(got[:m], op, dt, W, B, scope, x, what=f"n={n} B={B} scope={scope}")
             assert (got[m:] == POISON).all()
 
 
@@ -164,10 +189,9 @@ def test_block_reduce_persistent_path_and_compensation(cox, W, B):
                                    1 if comp else 0, lo.data_ptr(), None, 0, None) == 0
         want, wlo = o.reduce_emulate(o.SUM, o.F32, W, B, o.BLOCK, x, comp)
         np.testing.assert_array_equal(host(out), want)
-        _, ref, ab = o.reduce_ref(o.SUM, o.F32, B, x)
+        _check_reduce_def(host(out), o.SUM, o.F32, W, B, o.BLOCK, x, comp)
         if comp:
             np.testing.assert_array_equal(host(lo), wlo)
-            assert o.rel_err(host(out), ref, ab).max() <= TOL
     xi = inputs.bits_u32(n, seed=5).view(np.int32)
     got = host(cox.tile_reduce(dev(xi), o.SUM, W, B, o.BLOCK))
     np.testing.assert_array_equal(got, o.reduce_ref(o.SUM, o.I32, B, xi)[0])
@@ -181,6 +205,11 @@ def test_tile_reduce_compensated_low_word(cox, W):
     want, wlo = o.reduce_emulate(o.SUM, o.F32, W, 256, o.TILE, x, True)
     np.testing.assert_array_equal(host(out), want)
     np.testing.assert_array_equal(host(lo), wlo)
+    _check_reduce_def(host(out), o.SUM, o.F32, W, 256, o.TILE, x, comp=True)
+    # out + lo is the compensated pair's exact sum s + e: closer still to r
+    _, ref, ab = o.reduce_ref(o.SUM, o.F32, W, x)
+    pair = host(out).astype(np.float64) + host(lo).astype(np.float64)
+    assert o.rel_err(pair, ref, ab).max() <= fc.TOL
 
 
 @pytest.mark.parametrize("W", WIDTHS)
@@ -205,6 +234,7 @@ def test_tile_reduce_row_path_sizes_and_alignment(cox, W, comp):
                                        flags, lo.data_ptr() if comp else None, None, 0, None) == 0
             got = host(out)
             np.testing.assert_array_equal(got[:m].view(np.uint32), want.view(np.uint32))
+            _check_reduce_def(got[:m], o.SUM, o.F32, W, 256, o.TILE, x, comp, what=f"n={n} off={off}")
             assert (got[m:] == POISON).all()
             if comp:
                 np.testing.assert_array_equal(host(lo)[:m].view(np.uint32), wlo.view(np.uint32))
@@ -233,12 +263,14 @@ def test_block_reduce_row_path_tails_and_alignment(cox, W, B):
                                        cox.COX_F_COMPENSATED, lo.data_ptr(), None, 0, None) == 0
             got = host(out)
             np.testing.assert_array_equal(got[:m].view(np.uint32), want.view(np.uint32), err_msg=f"n={n} off={off}")
+            _check_reduce_def(got[:m], o.SUM, o.F32, W, B, o.BLOCK, x, True, what=f"n={n} off={off}")
             assert (got[m:] == POISON).all()
             np.testing.assert_array_equal(host(lo)[:m].view(np.uint32), wlo.view(np.uint32))
         xi = inputs.bits_u32(n, seed=n).view(np.int32)
         for op in (o.SUM, o.MIN, o.XOR):
             got = host(cox.tile_reduce(dev(xi), op, W, B, o.BLOCK))
             np.testing.assert_array_equal(got, o.reduce_emulate(op, o.I32, W, B, o.BLOCK, xi)[0])
+            _check_reduce_def(got, op, o.I32, W, B, o.BLOCK, xi)
     assert cox.device_status() == cox.COX_OK
 
 
@@ -252,10 +284,12 @@ def test_tile_reduce_2p26_fp32_full_size(cox, W):
         out, lo = got if comp else (got, None)
         want, wlo = o.reduce_emulate(o.SUM, o.F32, W, 256, o.TILE, x, comp)
         np.testing.assert_array_equal(host(out), want)
+        _check_reduce_def(host(out), o.SUM, o.F32, W, 256, o.TILE, x, comp, what="TILE 2^26")
         if comp:
             np.testing.assert_array_equal(host(lo), wlo)
         bo = cox.tile_reduce(xd, o.SUM, W, 256, o.BLOCK, compensated=comp)
         np.testing.assert_array_equal(host(bo), o.reduce_emulate(o.SUM, o.F32, W, 256, o.BLOCK, x, comp)[0])
+        _check_reduce_def(host(bo), o.SUM, o.F32, W, 256, o.BLOCK, x, comp, what="BLOCK 2^26")
 
 
 @pytest.mark.parametrize("dt,op", OPS)
@@ -292,6 +326,7 @@ def test_tile_scan_matches_the_emulation(cox, dt, op, W):
                                  None) == 0
         got = host(out)
         np.testing.assert_array_equal(got[:n].view(np.uint32), o.scan_emulate(op, dt, W, 256, x).view(np.uint32))
+        _check_scan_def(got[:n], op, dt, W, x, what=f"n={n}")
         assert (got[n:] == POISON).all()
 
 
@@ -317,6 +352,7 @@ def test_tile_scan_row_path_sizes_and_alignment(cox, W, comp):
             got = host(out)
             want = o.scan_emulate(o.SUM, o.F32, W, 256, x, comp)
             np.testing.assert_array_equal(got[off:off + n].view(np.uint32), want.view(np.uint32))
+            _check_scan_def(got[off:off + n], o.SUM, o.F32, W, x, comp, what=f"n={n} off={off}")
             assert (got[:off] == POISON).all() and (got[off + n:] == POISON).all()
     assert cox.device_status() == cox.COX_OK
 
@@ -328,8 +364,7 @@ def test_compensated_scan_bits_and_error(cox, W):
     for B in (64, 256, 1024):
         got = host(cox.tile_scan(dev(x), o.SUM, W, B, compensated=True))
         np.testing.assert_array_equal(got, o.scan_emulate(o.SUM, o.F32, W, B, x, True))
-    _, ref, ab = o.scan_ref(o.SUM, o.F32, W, x)
-    assert o.rel_err(got, ref, ab).max() <= TOL
+        _check_scan_def(got, o.SUM, o.F32, W, x, True, what=f"B={B}")
 
 
 # ------------------------------------------------------ cox_ballot_compact
@@ -433,13 +468,10 @@ def test_tile_scan_2p26_fp32_full_size(cox, W):
     n = 1 << 26
     x = inputs.normal_f32(n, seed=inputs.BASE_SEED + 1)
     xd = dev(x)
-    _, ref, ab = o.scan_ref(o.SUM, o.F32, W, x)
     for comp in (False, True):
         got = host(cox.tile_scan(xd, o.SUM, W, 256, compensated=comp))
         np.testing.assert_array_equal(got, o.scan_emulate(o.SUM, o.F32, W, 256, x, comp))
-        err = o.rel_err(got, ref, ab)
-        if comp:
-            assert err.max() <= TOL
+        _check_scan_def(got, o.SUM, o.F32, W, x, comp, what=f"W={W} comp={comp}")
 
 
 @pytest.mark.parametrize("d", [0.1, 0.5, 0.9])

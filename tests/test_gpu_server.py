@@ -12,6 +12,7 @@ import pytest
 
 import oracle as o
 from paper_2112_10034_gb300 import inputs
+from tests import fpcheck as fc
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -59,8 +60,11 @@ def make_mix(cox, count, seed, lo=1000, hi=1 << 18):
 def check_against_oracle(cox, req, host_in, got):
     g = got.cpu().numpy()
     if req.kind == cox.COX_REQ_SCAN:
-        want = o.scan_emulate(o.SUM, o.F32, req.width, 256, host_in, compensated=bool(req.flags & 1))
+        comp = bool(req.flags & 1)
+        want = o.scan_emulate(o.SUM, o.F32, req.width, 256, host_in, compensated=comp)
         np.testing.assert_array_equal(g, want)
+        _, ref, ab = o.scan_ref(o.SUM, o.F32, req.width, host_in)
+        fc.assert_fp64(g, ref, ab, comp, fc.tile_depth(req.width), "served scan")
     elif req.kind == cox.COX_REQ_COMPACT:
         want, cnt = o.ballot_compact(o.I32, 32, 256, host_in, req.threshold)
         assert g.size == cnt
@@ -96,6 +100,47 @@ def test_each_result_is_the_same_alone_and_in_the_mix(cox):
         assert srv.stats()["used_bytes"] == 0
     finally:
         srv.close()
+
+
+def test_full_size_mix_against_the_oracle(cox):
+    """Twenty requests of the serving workload's kinds with sizes up to 16M
+    elements (several at exactly 2^24, so large requests take many tiles and
+    deep look-backs inside one persistent launch), all submitted before any
+    completes so they share launches; every result must match the oracle and
+    the same request run alone."""
+    count = 20
+    mix = make_mix(cox, count, seed=31, lo=1024, hi=1 << 24)
+    import torch
+    n = 1 << 24  # one request of each kind at the top size
+    hs = [inputs.normal_f32(n, 41), inputs.uniform_int32(n, -1000, 1000, 42), inputs.normal_f32(n, 43),
+          inputs.uniform_u31(n, 44)]
+    kw = [dict(kind=cox.COX_REQ_REDUCE, compensated=True), dict(kind=cox.COX_REQ_REDUCE),
+          dict(kind=cox.COX_REQ_SCAN, compensated=True, width=32),
+          dict(kind=cox.COX_REQ_COMPACT, threshold=inputs.density_threshold(0.5))]
+    for h, r in zip(hs, kw):
+        d = torch.from_numpy(h).cuda()
+        mix.append((cox.make_request(r.pop("kind"), d, **r), d, h))
+    assert max(r.n for r, _, _ in mix) == 1 << 24
+    srv = cox.Server(6 << 30)
+    try:
+        tickets = [srv.submit(r, keep=d) for r, d, _ in mix]
+        for t in tickets:
+            srv.wait(t, timeout_s=120.0)
+        in_mix = [srv.result(t, r) for t, (r, _, _) in zip(tickets, mix)]
+        for t in tickets:
+            srv.release(t)
+        st = srv.stats()
+        assert st["completed"] == len(mix) and st["failed"] == 0
+        for (r, d, h), got in zip(mix, in_mix):
+            check_against_oracle(cox, r, h, got)
+            t = srv.submit(r, keep=d)
+            srv.wait(t, timeout_s=120.0)
+            alone = srv.result(t, r)
+            srv.release(t)
+            assert np.array_equal(alone.cpu().numpy().view(np.uint32), got.cpu().numpy().view(np.uint32))
+    finally:
+        srv.close()
+    assert cox.device_status() == cox.COX_OK
 
 
 def test_admission_respects_the_budget(cox):

@@ -46,11 +46,16 @@ def _with_workspace(cox, keys, n, t, block):
 
 
 def _static(cox, keys, n, t, block):
+    """Calls the static-scratch entry point; asserts that the call itself
+    took no memory from torch's caching allocator (the outputs are made
+    before it)."""
     import torch
     out = torch.full((n + 16,), -7, dtype=torch.int32, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    before = torch.cuda.memory_stats()["allocation.all.allocated"]
     assert cox.cox_ballot_compact_static(cox.COX_I32, 32, block, keys.data_ptr(), n, t, out.data_ptr(),
                                          cnt.data_ptr(), None) == cox.COX_OK
+    assert torch.cuda.memory_stats()["allocation.all.allocated"] == before
     return out, cnt
 
 
@@ -75,7 +80,7 @@ def test_input_beyond_the_fixed_scratch_is_refused(cox):
     import torch
     keys = torch.zeros(16, dtype=torch.int32, device="cuda")
     out = torch.zeros(16, dtype=torch.int32, device="cuda")
-    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    cnt = torch.full((1,), -1, dtype=torch.int64, device="cuda")  # a sentinel no run of the kernel leaves
     # 256 header bytes + 8 per tile of 16384 keys + 16 per group of 32 tiles: at most 123330 tiles
     limit = 123330 * 16384
     assert cox.cox_ballot_compact_workspace(limit, 256) <= cox.COX_COMPACT_STATIC_SCRATCH_BYTES
@@ -83,4 +88,5 @@ def test_input_beyond_the_fixed_scratch_is_refused(cox):
     st = cox.cox_ballot_compact_static(cox.COX_I32, 32, 256, keys.data_ptr(), limit + 1, 0, out.data_ptr(),
                                        cnt.data_ptr(), None)
     assert st == cox.COX_ENOMEM
-    assert int(cnt.item()) == 0  # nothing was enqueued
+    torch.cuda.synchronize()
+    assert int(cnt.item()) == -1  # nothing was enqueued: the count was neither cleared nor written
