@@ -305,13 +305,16 @@ size_t cox_integral_image_workspace(int64_t batch, int64_t height, int64_t width
  *   unless flags has COX_F_WS_READY, in which case the caller guarantees those
  *   bytes are zero.  Not shared across concurrent calls.
  *   flags: 0 or COX_F_WS_READY.
- * Tiles of 16384 keys (one CTA of 256 threads each, whatever block_dim: the
- * result does not depend on the block size, which is only validated) are
- * ordered by a ticket counter; each tile's look-back
- * polls its predecessors' descriptors.  A poll that exceeds the spin
- * limit (cox_set_spin_limit) gives up: the tile publishes a zero prefix, writes
- * nothing, and COX_ETIMEOUT is recorded for cox_device_status().  Every write
- * stays inside d_out[0, n) and d_count.
+ * Tiles of 8192 keys go round-robin to the CTAs of one cooperative launch
+ * (256 threads each, whatever block_dim: the result does not depend on the
+ * block size, which is only validated); each tile's look-back polls its
+ * predecessors' descriptors.  A poll that exceeds the spin limit
+ * (cox_set_spin_limit) gives up: the tile publishes a zero prefix, writes
+ * nothing, and COX_ETIMEOUT is recorded for cox_device_status().  With
+ * COX_F_WS_READY, a descriptor word whose two top bits are both set is
+ * "withheld": it reads as not yet published, and no publish overwrites it
+ * (a way to test that the waits end).  Every write stays inside d_out[0, n)
+ * and d_count.  COX_ECUDA if the cooperative launch is refused.
  */
 cox_status cox_ballot_compact(cox_dtype dt, int width, int block_dim, const void* d_keys, int64_t n,
                               int64_t threshold, void* d_out, int64_t* d_count, void* d_workspace,
@@ -332,8 +335,8 @@ size_t cox_ballot_compact_workspace(int64_t n, int block_dim);
  * flags.  The scratch is a fixed array of COX_COMPACT_STATIC_SCRATCH_BYTES
  * (1 MiB) inside libcox.so, held on every GPU that loads the library until
  * the process exits.  It fits 256 bytes of header, 8 bytes per tile of
- * 16384 keys and 16 bytes per group of 32 tiles: n <= 123330 * 16384
- * (2,020,638,720 keys).  Larger n returns COX_ENOMEM before anything is
+ * 8192 keys and 16 bytes per group of 32 tiles: n <= 123330 * 8192
+ * (1,010,319,360 keys).  Larger n returns COX_ENOMEM before anything is
  * enqueued.
  * The call allocates nothing (no cudaMalloc/cudaFree) and clears the scratch
  * bytes it uses with a cudaMemsetAsync on `stream` before its kernel.
@@ -356,14 +359,16 @@ cox_status cox_ballot_compact_static(cox_dtype dt, int width, int block_dim, con
  * cox_match_histogram -- histogram built from match_any peer groups.
  *
  * Per tile: peers = match_any(key) among the lanes whose key is in [0, bins);
- * the lowest lane of each peer group adds popc(peers) to a shared-memory bin;
+ * one lane of each peer group adds popc(peers) to a shared-memory bin;
  * blocks merge into d_hist.  Same family of warp functions as Section 2.2.1.
  * By default the peer mask comes from a per-warp table in shared memory
- * (each in-range lane ORs its lane bit into its key's word, then reads the
- * word back: the lanes holding that key) when two tables of `bins` words
+ * (each in-range lane ORs its lane bit into its key's word -- one word per
+ * key and tile of the warp -- and the lane whose OR found the word empty
+ * takes the mask and clears it) when two tables of (32 / width) * bins words
  * per warp fit next to the histograms, else from ceil(log2(bins)) + 1
  * ballots (lanes agree on a key iff they agree on every key bit); both are
- * exactly the mask __match_any_sync returns.  COX_F_BALLOT_MATCH forces the
+ * exactly the mask __match_any_sync returns, and one lane of each peer
+ * group adds its popcount.  COX_F_BALLOT_MATCH forces the
  * ballots; COX_F_NATIVE_MATCH takes the mask from the match.any.sync
  * instruction instead (same result, slower on sm_103a).
  * COX_F_DIRECT_ATOMICS skips the peer groups: every key adds one to its
@@ -396,7 +401,9 @@ typedef struct {
                         1 the match.any.sync instruction, 2 none (one shared atomic per key;
                         same counts, not built from match_any), 3 the match_any masks from a
                         per-warp table in shared memory (lanes OR their bit into their key's
-                        word and read it back) */
+                        word in their tile's copy of the table; the lane that found the word
+                        empty takes the mask and clears it), or from the ballots of 0 where
+                        that table (2 x 32 / width x 1 KB per warp) does not fit an SM */
 } cox_batch_tune;
 
 /* Bytes of device workspace for a batch of num_arrays arrays (any tune). */
@@ -493,6 +500,8 @@ typedef struct {
   size_t used_bytes;    /* held by admitted, unreleased requests */
   size_t peak_bytes;    /* most ever held */
   int64_t queued;       /* submitted, waiting for admission */
+  double wait_s;        /* summed over completed requests: submit to launch (queueing and batching) */
+  double run_s;         /* summed over completed requests: launch to done (on the device) */
 } cox_server_stats;
 
 /*
@@ -502,10 +511,14 @@ typedef struct {
  * queued requests in arrival order while the arena has room for their
  * output and workspace (plus their input, counted as held) and a slot is
  * free; it packs every admitted request not yet launched into one
- * persistent kernel -- each request cut into tiles of 4096 elements that
+ * persistent kernel -- each request cut into tiles of 16384 elements that
  * CTAs take from an atomic counter in request order -- on one of three
  * streams, so a batch launched while another runs overlaps with it on the
- * device; and it marks requests done when their batch's event fires.
+ * device (batches of up to 24 requests pass their table as a kernel
+ * parameter, larger ones copy it first); and it marks each request done as
+ * soon as the kernel raises that request's flag in pinned host memory --
+ * after its last tile's results are in device memory, without waiting for
+ * the rest of the batch -- or at the latest when the batch's event fires.
  * Each request's arithmetic depends only on the request (its tiles, its
  * fixed-order combine), never on what else shares its launch.
  */

@@ -497,7 +497,8 @@ class cox_trace_item(ctypes.Structure):
 class cox_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("max_batch", ctypes.c_int64), ("budget_bytes", ctypes.c_size_t),
-                ("used_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t), ("queued", ctypes.c_int64)]
+                ("used_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t), ("queued", ctypes.c_int64),
+                ("wait_s", ctypes.c_double), ("run_s", ctypes.c_double)]
 
     def asdict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -30,6 +30,7 @@ constexpr int kBatchBins = 256;
 constexpr int kBatchMaxCtas = 4096;
 constexpr size_t kBatchHeader = 256;
 constexpr cox_batch_tune kDefaultTune = {512, 2, 32, 8, 3};
+constexpr size_t kBatchSmemPerSm = 220 * 1024;  // dynamic shared memory the CTAs of one SM may take
 
 __host__ __device__ __forceinline__ int64_t cta_begin(int64_t i, int64_t E, int64_t G) {
   return (int64_t)(((uint64_t)i * (uint64_t)E) / (uint64_t)G);
@@ -42,33 +43,28 @@ __device__ __forceinline__ int64_t cta_of(int64_t pos, int64_t E, int64_t G) {
 }
 
 // Histogram step of one warp: peers among the lane's width-W tile with the
-// same in-range key; the lowest peer adds the group's size to the warp's bins.
-// PEER: 0 the match_any mask from 9 ballots over the key bits, 1 the
-// match.any.sync instruction, 3 a per-warp table in shared memory (each
-// in-range lane ORs its lane bit into its key's word and reads the word back;
-// two tables used in turn, each word cleared by its key's lowest lane after
-// every lane has read it) -- the same mask every way; 2 no peer groups (one
-// shared atomic per key; same counts).
-template <int W, int PEER>
-__device__ __forceinline__ void batch_hist_step(uint32_t key, bool valid, uint32_t* my, uint32_t* tab, int& tsel) {
+// same in-range key; one lane of each peer group adds the group's size to
+// the warp's bins.  PEER: 0 the match_any mask from 9 ballots over the key
+// bits, 1 the match.any.sync instruction, 3 per-warp tables of masks in
+// shared memory (hist_peer_table: lanes OR their bit into their key's word;
+// the lane that found it empty takes the mask and clears the word) -- the
+// same mask every way; 2 no peer groups (one shared atomic per key; same
+// counts).
+template <int W, int PEER, int S>
+__device__ __forceinline__ void batch_hist_step(uint32_t key, bool valid, uint32_t* my, uint32_t* tab, int& parity) {
   const int lane = lane_id();
   const bool in = valid && key < (uint32_t)kBatchBins;
   if constexpr (PEER == 2) {
     if (in) atomicAdd(my + key, 1u);
+  } else if constexpr (PEER == 3) {
+    const uint32_t k1[1] = {key};
+    const bool in1[1] = {in};
+    hist_peer_table<W, 1, 1, false, S>(k1, in1, kBatchBins, my, tab, parity);  // the first table of a set
   } else {
     const unsigned tmask = W == 32 ? kFull : (((1u << W) - 1u) << (lane & ~(W - 1)));
     const unsigned lt = lanemask_lt();
     unsigned peers;
-    if constexpr (PEER == 3) {
-      uint32_t* t = tab + tsel * kBatchBins;
-      tsel ^= 1;
-      if (in) atomicOr(t + key, 1u << lane);
-      __syncwarp();
-      const unsigned all = in ? t[key] : 0u;
-      __syncwarp();
-      if (in && (all & lt) == 0u) t[key] = 0u;
-      peers = all;
-    } else if constexpr (PEER == 1) {
+    if constexpr (PEER == 1) {
       peers = __match_any_sync(kFull, key) & __ballot_sync(kFull, in);
     } else {
       peers = match_any_bits<8>(key, in);
@@ -78,14 +74,33 @@ __device__ __forceinline__ void batch_hist_step(uint32_t key, bool valid, uint32
   }
 }
 
+// Four keys of one lane; S peer tables serve S keys per round (PEER 3).
+template <int W, int PEER, int S>
+__device__ __forceinline__ void batch_hist_quad(const uint32_t* key, const bool* ok, uint32_t* my, uint32_t* tab,
+                                                int& parity) {
+  if constexpr (PEER == 3) {
+    uint32_t k4[4];
+    bool in4[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      k4[j] = key[j];
+      in4[j] = ok[j] && key[j] < (uint32_t)kBatchBins;
+    }
+    hist_peer_table<W, S, 4, false>(k4, in4, kBatchBins, my, tab, parity);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) batch_hist_step<W, PEER, S>(key[j], ok[j], my, tab, parity);
+  }
+}
+
 __device__ __forceinline__ void fold(Pair& acc, float x) { acc = Comp::op(acc, Comp::load(x)); }
 
 // One segment [s0, s1) of one array, all warps of the CTA.  Warp-uniform
 // loops: every lane of a warp runs every match_any step (invalid lanes take
 // part with valid = false).
-template <int W, int PEER>
+template <int W, int PEER, int S>
 __device__ void batch_segment(const float* __restrict__ v, const int32_t* __restrict__ k, int64_t s0, int64_t s1,
-                              Pair& acc, uint32_t* my, uint32_t* tab, int& tsel) {
+                              Pair& acc, uint32_t* my, uint32_t* tab, int& parity) {
   const int lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uintptr_t pv = reinterpret_cast<uintptr_t>(v), pk = reinterpret_cast<uintptr_t>(k);
   // 128-bit loads need values and keys at the same phase modulo 16 bytes
@@ -97,7 +112,7 @@ __device__ void batch_segment(const float* __restrict__ v, const int32_t* __rest
       const float x = ok ? __ldcs(v + e) : 0.0f;
       const uint32_t key = ok ? (uint32_t)__ldcs(k + e) : 0u;
       if (ok) fold(acc, x);
-      batch_hist_step<W, PEER>(key, ok, my, tab, tsel);
+      batch_hist_step<W, PEER, S>(key, ok, my, tab, parity);
     }
     return;
   }
@@ -112,7 +127,7 @@ __device__ void batch_segment(const float* __restrict__ v, const int32_t* __rest
     const float x = ok ? __ldcs(v + e) : 0.0f;
     const uint32_t key = ok ? (uint32_t)__ldcs(k + e) : 0u;
     if (ok) fold(acc, x);
-    batch_hist_step<W, PEER>(key, ok, my, tab, tsel);
+    batch_hist_step<W, PEER, S>(key, ok, my, tab, parity);
   }
   // body: warp steps of 128 elements (one 128-bit load of values and of keys
   // per lane), two steps in flight
@@ -141,26 +156,26 @@ __device__ void batch_segment(const float* __restrict__ v, const int32_t* __rest
       }
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < 8; ++j)
       if (ok[j]) fold(acc, x[j]);
-      batch_hist_step<W, PEER>(key[j], ok[j], my, tab, tsel);
-    }
+    batch_hist_quad<W, PEER, S>(key, ok, my, tab, parity);
+    batch_hist_quad<W, PEER, S>(key + 4, ok + 4, my, tab, parity);
   }
 }
 
-template <int W, int PEER>
+template <int W, int PEER, int S>
 __global__ void __launch_bounds__(1024) k_batch_sum_hist(const float* const* __restrict__ vals,
                                                          const int32_t* const* __restrict__ keys,
                                                          const int64_t* __restrict__ off, int64_t A,
                                                          float2* __restrict__ part, int32_t* __restrict__ hists) {
-  extern __shared__ uint32_t sh[];  // (blockDim / 32) x 256 per-warp bins, then the peer tables
+  extern __shared__ __align__(16) uint32_t sh[];  // (blockDim / 32) x 256 per-warp bins, then the peer tables
   __shared__ Pair wpart[32];
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
-  const int ntab = PEER == 3 ? nw * 2 * kBatchBins : 0;
-  for (int i = threadIdx.x; i < nw * kBatchBins + ntab; i += blockDim.x) sh[i] = 0u;
+  const int ntab = PEER == 3 ? 2 * S * (int)hist_table_words(W, kBatchBins, false) : 0;  // peer tables per warp
+  for (int i = threadIdx.x; i < nw * (kBatchBins + ntab); i += blockDim.x) sh[i] = 0u;
   __syncthreads();
-  uint32_t* tab = sh + nw * kBatchBins + warp * 2 * kBatchBins;
-  int tsel = 0;
+  uint32_t* tab = sh + nw * kBatchBins + warp * ntab;
+  int parity = 0;
   const int64_t E = off[A];
   const int64_t G = gridDim.x;
   const int64_t lo = cta_begin(blockIdx.x, E, G), hi = cta_begin(blockIdx.x + 1, E, G);
@@ -179,7 +194,7 @@ __global__ void __launch_bounds__(1024) k_batch_sum_hist(const float* const* __r
     const int64_t base = off[a];
     const int64_t end = min(hi, off[a + 1]);
     Pair acc = Comp::ident();
-    batch_segment<W, PEER>(vals[a], keys[a], pos - base, end - base, acc, my, tab, tsel);
+    batch_segment<W, PEER, S>(vals[a], keys[a], pos - base, end - base, acc, my, tab, parity);
     const Pair s = block_reduce32<Comp>(acc, wpart);  // ends with __syncthreads
     if (threadIdx.x == 0) part[a + blockIdx.x] = make_float2(s.s, s.e);
     for (int b = threadIdx.x; b < kBatchBins; b += blockDim.x) {
@@ -249,6 +264,21 @@ BatchWs batch_layout(void* ws, int64_t A) {
   return w;
 }
 
+template <int W, int PEER, int S>
+cox_status launch_batch(int G, int block_dim, size_t smem, cudaStream_t st, const float* const* d_vals,
+                        const int32_t* const* d_keys, const BatchWs& w, int64_t num_arrays, int32_t* d_hists) {
+  auto k = k_batch_sum_hist<W, PEER, S>;
+  static size_t attr[kMaxDevices];  // per device: the dynamic shared size this kernel may take so far
+  size_t& a = attr[device_index()];
+  if (smem > a) {  // (static shared memory counts against the 48 KB default too)
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return COX_ECUDA;
+    a = smem;
+  }
+  k<<<G, block_dim, smem, st>>>(d_vals, d_keys, w.off, num_arrays, w.part, d_hists);
+  return launch_status();
+}
+
 }  // namespace cox
 
 using namespace cox;
@@ -291,26 +321,29 @@ extern "C" cox_status cox_batch_sum_hist(int64_t num_arrays, const float* const*
   if (G > kBatchMaxCtas) G = kBatchMaxCtas;
   if (cudaMemsetAsync(d_hists, 0, (size_t)num_arrays * kBatchBins * sizeof(int32_t), st) != cudaSuccess)
     return COX_ECUDA;
-  const size_t smem = (size_t)(t.block_dim / 32) * kBatchBins * sizeof(uint32_t) *
-                      (t.native_match == 3 ? 3 : 1);  // per-warp bins (+ two peer tables)
+  // per-warp bins, then the peer tables (two sets of S tables of
+  // hist_table_words words per warp): four per set where that leaves room for
+  // ctas_per_sm CTAs on an SM, else two, else one
+  const size_t bins_bytes = (size_t)(t.block_dim / 32) * kBatchBins * sizeof(uint32_t);
+  const size_t tab_bytes =  // one table of each of the two sets
+      (size_t)(t.block_dim / 32) * 2 * hist_table_words(t.width, kBatchBins, false) * sizeof(uint32_t);
+  // (tables that do not fit one SM at all: the same masks from ballots)
+  const int peer = t.native_match == 3 && bins_bytes + tab_bytes > kBatchSmemPerSm ? 0 : t.native_match;
+  int tables = 0;
+  if (peer == 3)
+    for (tables = 4; tables > 1 && (bins_bytes + tables * tab_bytes) * (size_t)t.ctas_per_sm > kBatchSmemPerSm;)
+      tables >>= 1;
+  const size_t smem = bins_bytes + (size_t)tables * tab_bytes;
   const cox_status s = with_width(t.width, [&](auto wc) {
     constexpr int W = decltype(wc)::value;
-    if (t.native_match == 3) {
-      auto k = k_batch_sum_hist<W, 3>;
-      static bool attr = false;  // up to 96 KB of shared memory
-      if (!attr) {
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024) != cudaSuccess)
-          return COX_ECUDA;
-        attr = true;
-      }
-      k<<<G, t.block_dim, smem, st>>>(d_vals, d_keys, w.off, num_arrays, w.part, d_hists);
-    } else if (t.native_match == 1)
-      k_batch_sum_hist<W, 1><<<G, t.block_dim, smem, st>>>(d_vals, d_keys, w.off, num_arrays, w.part, d_hists);
-    else if (t.native_match == 2)
-      k_batch_sum_hist<W, 2><<<G, t.block_dim, smem, st>>>(d_vals, d_keys, w.off, num_arrays, w.part, d_hists);
-    else
-      k_batch_sum_hist<W, 0><<<G, t.block_dim, smem, st>>>(d_vals, d_keys, w.off, num_arrays, w.part, d_hists);
-    return launch_status();
+    if (peer == 3 && tables == 4)
+      return launch_batch<W, 3, 4>(G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
+    if (peer == 3 && tables == 2)
+      return launch_batch<W, 3, 2>(G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
+    if (peer == 3) return launch_batch<W, 3, 1>(G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
+    if (peer == 1) return launch_batch<W, 1, 1>(G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
+    if (peer == 2) return launch_batch<W, 2, 1>(G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
+    return launch_batch<W, 0, 1>(G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
   });
   if (s != COX_OK) return s;
   const int cb = 256;

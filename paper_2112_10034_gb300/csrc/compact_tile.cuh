@@ -5,20 +5,16 @@
 // static, full-warp group instead of the dynamically coalesced one (the paper
 // covers non-divergent warp functions only, Section 2.2.3):
 //   b = __ballot_sync(full, key < t); rank = popc(b & lanemask_lt);
-// a shared-memory scan orders the warps of a tile, and tiles are ordered by
-// a single-pass decoupled look-back over per-tile descriptors.  A tile only
+// a shared-memory scan orders the warps of a tile, and tiles are ordered by a
+// single-pass decoupled look-back over per-tile descriptors.  A tile only
 // waits on tiles with smaller indexes, which callers hand out in order to
 // CTAs that already run, so the waits end; each wait is still bounded.
 // The look-back has two levels: within a group of 32 tiles, then over whole
 // groups (their counts summed by atomics as the last tile of each arrives).
 //
-// Tile layout: a tile of kBigTile = 16384 keys sits in shared memory.  Warp
-// w of pass j owns the run of 512 keys at 16Bj + 512w; its lanes read them
-// as four 128-bit chunks, lane l holding keys 128q + 4l .. 128q + 4l + 3 of
-// chunk q.  The rank of a kept key in the tile is
-//   offset(j, w) + kept keys of earlier chunks of the run
-//     + sum_k' popc(ballot_k'(q) & lanemask_lt) + kept keys before it in the lane,
-// which is its position in input order, so the result is the stable filter.
+// Tile layout: a tile of NW * 2048 keys sits in shared memory; warp w owns
+// the region of keys [2048w, 2048w + 2048) and compacts it in place to the
+// region's front in one pass, then copies it out after the look-back.
 #pragma once
 
 #include "cox_common.cuh"
@@ -29,6 +25,18 @@ constexpr size_t kCompactWsHeader = 256;
 constexpr uint64_t kFlagA = 1ull << 62;  // descriptor holds the tile's own count
 constexpr uint64_t kFlagP = 2ull << 62;  // descriptor holds the inclusive prefix
 constexpr uint64_t kValMask = (1ull << 62) - 1;
+// Flags 0 (nothing yet) and 3 (withheld) both read as "not published".
+// Descriptors only ever grow (atomicMax: A < P < withheld), so a word a
+// caller withheld in a zeroed workspace (COX_F_WS_READY) stays withheld; the
+// library never writes one itself -- tests use it to make a look-back wait
+// run out.
+__device__ __forceinline__ bool desc_missing(uint64_t d) {
+  const uint64_t f = d >> 62;
+  return f == 0 || f == 3;
+}
+__device__ __forceinline__ void desc_raise(uint64_t* p, uint64_t v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
 
 // Two-level decoupled look-back over tile counts.  Tiles form groups of 32
 // (group g = tiles 32g .. 32g+31).  Next to the per-tile descriptors
@@ -54,7 +62,7 @@ constexpr uint64_t kGroupSumMask = kGroupArrive - 1;
 __host__ __device__ inline int64_t compact_groups(int64_t ntiles) {
   return (ntiles + (1 << kGroupShift) - 1) >> kGroupShift;
 }
-// Workspace bytes of a compaction over ntiles tiles: header (ticket), tile
+// Workspace bytes of a compaction over ntiles tiles: a header (reserved), tile
 // descriptors, group descriptors and group accumulators.
 __host__ __device__ inline size_t compact_ws_bytes(int64_t ntiles) {
   return kCompactWsHeader + (size_t)ntiles * 8 + (size_t)compact_groups(ntiles) * 16;
@@ -62,7 +70,7 @@ __host__ __device__ inline size_t compact_ws_bytes(int64_t ntiles) {
 
 // Publishes a tile's own count (lane 0 of the looking-back warp).
 __device__ __forceinline__ void publish_count(uint64_t* desc, int64_t tile, int64_t ntiles, uint32_t total) {
-  st_relaxed_u64(desc + tile, (tile == 0 ? kFlagP : kFlagA) | total);
+  desc_raise(desc + tile, (tile == 0 ? kFlagP : kFlagA) | total);
   uint64_t* gdesc = desc + ntiles;
   uint64_t* gacc = gdesc + compact_groups(ntiles);
   const int64_t g = tile >> kGroupShift;
@@ -94,7 +102,7 @@ __device__ __forceinline__ int64_t look_back(uint64_t* desc, int64_t tile, int64
     for (;;) {
       pm = __ballot_sync(kFull, lane < pos && (d >> 62) == 2);
       fl = pm ? 31 - __clz(pm) : -1;  // closest inclusive prefix: the highest position
-      const bool missing = lane < pos && lane > fl && (d >> 62) == 0;
+      const bool missing = lane < pos && lane > fl && desc_missing(d);
       if (!__any_sync(kFull, missing)) break;
       if (++polls > limit) {
         timed_out = true;
@@ -120,7 +128,7 @@ __device__ __forceinline__ int64_t look_back(uint64_t* desc, int64_t tile, int64
       for (;;) {
         pm = __ballot_sync(kFull, (d >> 62) == 2);
         const int fl = pm ? __ffs(pm) - 1 : 32;  // closest group with an inclusive prefix
-        const bool missing = lane <= fl && (d >> 62) == 0;
+        const bool missing = lane <= fl && desc_missing(d);
         if (!__any_sync(kFull, missing)) break;
         if (++polls > limit) {
           timed_out = true;
@@ -142,27 +150,27 @@ __device__ __forceinline__ int64_t look_back(uint64_t* desc, int64_t tile, int64
     gave_up = true;
     if (lane == 0) {
       atomicOr(status, (unsigned)kDevTimeout);
-      st_relaxed_u64(desc + tile, kFlagP);  // release successors with a zero prefix
+      desc_raise(desc + tile, kFlagP);  // release successors with a zero prefix
       if (pos == (1 << kGroupShift) - 1) atomicMax(reinterpret_cast<unsigned long long*>(gdesc + g), kFlagP);
     }
     return 0;
   }
   if (lane == 0) {
     const uint64_t inc = kFlagP | ((uint64_t)(prefix + total) & kValMask);
-    if (tile != 0) st_relaxed_u64(desc + tile, inc);
+    if (tile != 0) desc_raise(desc + tile, inc);
     if (pos == (1 << kGroupShift) - 1) atomicMax(reinterpret_cast<unsigned long long*>(gdesc + g), inc);
   }
   return prefix;
 }
 
 // ------------------------------------------------------------ big tiles
-// Compaction of one tile of up to kBigTile keys already in shared memory
-// (`buf`, valid keys at [0, valid)), with the whole CTA of B threads
-// (16 * B divides kBigTile).  `wcnt` holds kBigTile / 512 words.  Counts
-// with redux.sync, publishes the tile's count, compacts in place (a key's
-// rank never exceeds its index), looks back for the prefix and copies the
-// kept keys to out[prefix ..]; the last tile writes *d_count.
-constexpr int64_t kBigTile = 16384;  // keys per tile (64 KB); 16 * block_dim divides it for every block_dim
+// Compaction of one tile of up to NW * 2048 keys already in shared memory
+// (`buf`, valid keys at [0, valid)), by a CTA of NW warps.  `wcnt` holds
+// kCompactWsWords words.  Each warp compacts its region in place, the tile's
+// count is published, the look-back finds the tile's prefix, and every warp
+// copies its kept keys to out[prefix + the warps before it ..]; the last
+// tile writes *d_count.
+constexpr int64_t kBigTile = 16384;  // elements per tile of the request server (64 KB)
 
 // key < thr as one 32-bit compare: thr is clamped into the key range first
 // (every key passes if thr is above the range, none if at or below it).
@@ -186,145 +194,147 @@ __device__ __forceinline__ bool keep_key(uint32_t k, KeepRule r) {
   return r.mode == 0 ? lt : r.mode == 1;
 }
 
-// The count and compact passes over one tile; FULL tiles skip bounds checks.
-// Pass j covers keys [16Bj, 16B(j+1)) of the tile; warp w owns the run
-// [16Bj + 512w, + 512) of it, lane l holding keys 128q + 4l .. + 3 of the run
-// for chunks q = 0..3 (128-bit shared loads, no bank conflicts).  Order of a
-// tile: pass, warp, chunk, lane, key -- which is input order.
-template <bool FULL>
-__device__ __forceinline__ int run_index(int j, int B, int warp, int q, int lane) {
-  return 16 * B * j + 512 * warp + 128 * q + 4 * lane;
-}
+// key < thr as one compare, key <= tm, in the key's own signedness: tm =
+// thr - 1 clamped into the key range; `none` when thr is at or below the
+// range's bottom (no key is kept).
+struct LeRule {
+  uint32_t tm;
+  bool none;
+};
 
-// Count: each lane counts its kept keys, redux.sync gives the warp's count.
-template <bool SIGNED, bool FULL>
-__device__ __forceinline__ void count_pass(const uint32_t* buf, int j, int B, int nw, int warp, int lane,
-                                           int valid, KeepRule r, uint32_t* wcnt) {
-  uint32_t c = 0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i0 = run_index<FULL>(j, B, warp, q, lane);
-    const uint4 v = *reinterpret_cast<const uint4*>(buf + i0);
-    c += (FULL || i0 + 0 < valid) && keep_key<SIGNED>(v.x, r);
-    c += (FULL || i0 + 1 < valid) && keep_key<SIGNED>(v.y, r);
-    c += (FULL || i0 + 2 < valid) && keep_key<SIGNED>(v.z, r);
-    c += (FULL || i0 + 3 < valid) && keep_key<SIGNED>(v.w, r);
-  }
-  c = __reduce_add_sync(kFull, c);
-  if (lane == 0) wcnt[j * nw + warp] = c;
-}
-
-// Compact: rank = warp offset + kept keys of earlier chunks of the run +
-// popc(ballot & lanemask_lt) over the chunk's four key slots + kept keys
-// before it in the lane; every kept key moves to buf[rank].
-template <bool SIGNED, bool FULL>
-__device__ __forceinline__ void compact_pass(uint32_t* buf, int j, int B, int nw, int warp, int lane, int valid,
-                                             KeepRule r, const uint32_t* wcnt, unsigned lt) {
-  uint32_t key[4][4], pos[4][4];
-  bool kp[4][4];
-  uint32_t base = wcnt[j * nw + warp];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i0 = run_index<FULL>(j, B, warp, q, lane);
-    const uint4 v = *reinterpret_cast<const uint4*>(buf + i0);
-    key[q][0] = v.x; key[q][1] = v.y; key[q][2] = v.z; key[q][3] = v.w;
-    uint32_t o = base, chunk = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      kp[q][k] = (FULL || i0 + k < valid) && keep_key<SIGNED>(key[q][k], r);
-      const unsigned b = __ballot_sync(kFull, kp[q][k]);
-      o += __popc(b & lt);
-      chunk += __popc(b);
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {  // o = rank of this lane's first kept key in chunk q
-      pos[q][k] = o;
-      o += kp[q][k];
-    }
-    base += chunk;
-  }
-  __syncthreads();  // every read of pass j before any write of pass j
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (kp[q][k]) buf[pos[q][k]] = key[q][k];
+template <bool SIGNED>
+__host__ __device__ inline LeRule le_rule(int64_t thr) {
+  const int64_t lo = SIGNED ? -(int64_t(1) << 31) : 0;
+  const int64_t hi = SIGNED ? (int64_t(1) << 31) - 1 : (int64_t(1) << 32) - 1;
+  if (thr <= lo) return {0u, true};
+  return {(uint32_t)(thr - 1 > hi ? hi : thr - 1), false};
 }
 
 template <bool SIGNED>
+__device__ __forceinline__ bool keep_le(uint32_t k, uint32_t tm) {
+  return SIGNED ? (int32_t)k <= (int32_t)tm : k <= tm;
+}
+
+// The tile body runs NW warps per CTA on a tile of NW * 2048 keys: each warp
+// owns a region of 2048 keys, which it reads as four sub-runs of 512 (lane l
+// holds keys 128q + 4l .. 128q + 4l + 3 of a sub-run, q = 0..3:
+// conflict-free 128-bit shared loads).
+constexpr int kCompactRegion = 2048;  // keys per warp
+constexpr int kCompactWsWords = 2 * 32;  // shared words the tile body needs (counts, offsets), any NW <= 32
+
+// One sub-run of a warp's region, compacted in place to the front of the
+// region.  Per chunk q and key slot k every lane votes b = __ballot_sync(keep);
+// a kept key's rank in the region is
+//   kept keys of earlier sub-runs and chunks + sum_k' popc(b_k' & lanes below)
+//     + kept keys before it in its lane,
+// i.e. its position in input order.  Ranks never exceed the key's own index,
+// so the writes only reach keys every lane has already loaded (the
+// __syncwarp after the loads orders them).  Returns the sub-run's count.
+template <bool SIGNED, bool FULL>
+__device__ __forceinline__ uint32_t compact_subrun(uint32_t* buf, int region, int sub, int lane, unsigned lt,
+                                                   int valid, uint32_t tm, uint32_t kept_before) {
+  const int sb = region + 512 * sub;
+  uint32_t key[4][4];
+  bool kp[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i0 = sb + 128 * q + 4 * lane;
+    const uint4 v = *reinterpret_cast<const uint4*>(buf + i0);
+    key[q][0] = v.x; key[q][1] = v.y; key[q][2] = v.z; key[q][3] = v.w;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) kp[q][k] = (FULL || i0 + k < valid) && keep_le<SIGNED>(key[q][k], tm);
+  }
+  uint32_t below[4], total[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    below[q] = 0;
+    total[q] = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const unsigned b = __ballot_sync(kFull, kp[q][k]);
+      below[q] += __popc(b & lt);
+      total[q] += __popc(b);
+    }
+  }
+  __syncwarp();  // every lane's loads of this sub-run before any write into it
+  uint32_t chunk_base = kept_before;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t* o = buf + region + chunk_base + below[q];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (kp[q][k]) *o = key[q][k];
+      o += kp[q][k];
+    }
+    chunk_base += total[q];
+  }
+  return chunk_base - kept_before;
+}
+
+// A warp's region of REG keys (a multiple of 512) compacted in place to its
+// front, sub-run by sub-run; returns the region's count.
+template <bool SIGNED, int REG>
+__device__ __forceinline__ uint32_t compact_region(uint32_t* buf, int region, int lane, unsigned lt, int valid,
+                                                   bool full, LeRule rule) {
+  uint32_t kept = 0;
+  if (rule.none) return 0;
+  if (full) {
+#pragma unroll 1
+    for (int sub = 0; sub < REG / 512; ++sub)
+      kept += compact_subrun<SIGNED, true>(buf, region, sub, lane, lt, valid, rule.tm, kept);
+  } else {
+#pragma unroll 1
+    for (int sub = 0; sub < REG / 512 && region + 512 * sub < valid; ++sub)
+      kept += compact_subrun<SIGNED, false>(buf, region, sub, lane, lt, valid, rule.tm, kept);
+  }
+  return kept;
+}
+
+template <bool SIGNED, int NW>
 __device__ __forceinline__ void compact_big_tile(uint32_t* buf, int valid, int64_t thr, uint32_t* __restrict__ out,
                                                  int64_t* __restrict__ d_count, uint64_t* desc, int64_t tile,
                                                  int64_t ntiles, int64_t n, uint32_t limit, unsigned* status,
                                                  uint32_t* wcnt) {
-  const int B = blockDim.x, nw = B >> 5;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t TILE = kBigTile;
-  const int passes = (int)(TILE / (16 * B));
-  const int m = passes * nw;
+  const int region = warp * kCompactRegion;
   __shared__ int64_t s_prefix;
   __shared__ uint32_t s_total;
   __shared__ int s_bad;
-  // ---- count: pass j, chunk q holds keys j*16B + q*4B + 4t .. + 3
-  const KeepRule rule = keep_rule<SIGNED>(thr);
-  const int vlen = valid;
-#pragma unroll 1
-  for (int j = 0; j < passes; ++j) {
-    if (valid == TILE) count_pass<SIGNED, true>(buf, j, B, nw, warp, lane, vlen, rule, wcnt);
-    else count_pass<SIGNED, false>(buf, j, B, nw, warp, lane, vlen, rule, wcnt);
-  }
+  // ---- compact each warp's region in place (one pass over the keys)
+  const LeRule rule = le_rule<SIGNED>(thr);
+  const uint32_t kept =
+      compact_region<SIGNED, kCompactRegion>(buf, region, lane, lanemask_lt(), valid, valid == NW * kCompactRegion, rule);
+  if (lane == 0) wcnt[warp] = kept;
   __syncthreads();
-  // ---- scan of the m = 32 counts (one per lane) and the tile's count
+  // ---- the tile's count, its prefix by look-back, the warps' offsets
   if (warp == 0) {
-    const int per = (m + 31) / 32;
-    uint32_t sum = 0;
-    for (int k = 0; k < per; ++k) {
-      const int idx = lane * per + k;
-      if (idx < m) sum += wcnt[idx];
-    }
-    uint32_t incl = sum;
+    const uint32_t c = lane < NW ? wcnt[lane] : 0u;
+    uint32_t incl = c;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
+    for (int d = 1; d < NW; d <<= 1) {
       const uint32_t u = __shfl_up_sync(kFull, incl, d);
       if (lane >= d) incl += u;
     }
-    uint32_t ex = incl - sum;
-    for (int k = 0; k < per; ++k) {
-      const int idx = lane * per + k;
-      if (idx < m) {
-        const uint32_t c = wcnt[idx];
-        wcnt[idx] = ex;
-        ex += c;
-      }
-    }
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    if (lane == 0) {
-      publish_count(desc, tile, ntiles, total);
-      s_total = total;
-    }
-  }
-  __syncthreads();
-  // ---- compact in place, pass by pass
-  const unsigned lt = lanemask_lt();
-#pragma unroll 1
-  for (int j = 0; j < passes; ++j) {
-    if (valid == TILE) compact_pass<SIGNED, true>(buf, j, B, nw, warp, lane, vlen, rule, wcnt, lt);
-    else compact_pass<SIGNED, false>(buf, j, B, nw, warp, lane, vlen, rule, wcnt, lt);
-  }
-  // ---- prefix and copy-out
-  if (warp == 0) {
+    const uint32_t total = __shfl_sync(kFull, incl, NW - 1);
+    if (lane < NW) wcnt[32 + lane] = incl - c;  // exclusive offsets
+    if (lane == 0) publish_count(desc, tile, ntiles, total);
     bool gave_up;
-    const int64_t prefix = look_back(desc, tile, ntiles, s_total, limit, status, gave_up);
+    const int64_t prefix = look_back(desc, tile, ntiles, total, limit, status, gave_up);
     if (lane == 0) {
       s_prefix = prefix;
+      s_total = total;
       s_bad = gave_up;
     }
   }
   __syncthreads();
   const int64_t prefix = s_prefix;
-  const uint32_t total = s_total;
-  if (s_bad || prefix + (int64_t)total > n) return;
-  for (int i = tid; i < (int)total; i += B) out[prefix + i] = buf[i];
-  if (tile == ntiles - 1 && tid == 0) *d_count = prefix + total;
+  if (s_bad || prefix + (int64_t)s_total > n) return;
+  // ---- each warp copies its compacted region to out[prefix + offset ..]
+  uint32_t* dst = out + prefix + wcnt[32 + warp];
+  const uint32_t* src = buf + region;
+#pragma unroll 4
+  for (int i = lane; i < (int)kept; i += 32) dst[i] = src[i];
+  if (tile == ntiles - 1 && tid == 0) *d_count = prefix + s_total;
 }
 
 }  // namespace cox

@@ -253,6 +253,72 @@ __device__ __forceinline__ unsigned match_any_bits(uint32_t key, bool in) {
   return peers;
 }
 
+// Match-histogram step for NK keys per lane with peer groups from a table
+// in shared memory (S tables per round, all zero at the kernel's start).  In
+// a round every in-range lane ORs its lane bit into its key's word of its
+// tile; after a __syncwarp the words hold exactly the masks __match_any_sync
+// returns within each tile.  A lane whose OR found its word empty takes the
+// mask with an atomic exchange that also clears it, and adds the mask's
+// popcount to the key's bin.  Two layouts:
+//   SPLIT   (hist_table_words(W, bins, true) words per table, S tables):
+//           at width 32 a key's mask is split over two adjacent words --
+//           lanes 0-15 OR into the first, lanes 16-31 into the second --
+//           which halves the lanes that hit one address on a hot key (shared
+//           atomics on one address are serialised); the first lane of each
+//           half swaps the pair out as one 64-bit word, so the first swap
+//           takes the whole mask and a later one finds zero and adds
+//           nothing.  A second __syncwarp orders a round's exchanges before
+//           the next round's ORs.
+//   !SPLIT  (2 x SET tables of hist_table_words(W, bins, false) words): one
+//           word per key and tile, and the rounds alternate between two sets
+//           of SET tables (a round uses the first S of its set), so one
+//           __syncwarp per round suffices: a round's ORs follow the previous
+//           round's __syncwarp, which every lane reaches only after its
+//           exchanges of the round before.
+// Below width 32 every tile of the warp has its own words (word tile * bins
+// + key), so one lane per peer group finds its word empty.
+__host__ __device__ constexpr uint32_t hist_table_words(int W, uint32_t bins, bool split) {
+  return W == 32 ? (split ? 2 : 1) * bins : (uint32_t)(32 / W) * bins;
+}
+
+template <int W, int S, int NK, bool SPLIT, int SET = S>
+__device__ __forceinline__ void hist_peer_table(const uint32_t (&key)[NK], const bool (&in)[NK], uint32_t bins,
+                                                uint32_t* my, uint32_t* tab, int& parity) {
+  static_assert(NK % S == 0 && S <= SET, "S tables serve S keys per round; a set holds SET tables");
+  constexpr bool kSplit = SPLIT && W == 32;
+  const int lane = lane_id();
+  const uint32_t words = hist_table_words(W, bins, SPLIT);
+#pragma unroll
+  for (int q0 = 0; q0 < NK; q0 += S) {
+    uint32_t* t = tab;
+    if constexpr (!SPLIT) {
+      t += (uint32_t)parity * SET * words;
+      parity ^= 1;
+    }
+    uint32_t old[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const uint32_t w = kSplit ? 2 * key[q0 + s] + (uint32_t)(lane >> 4) : (uint32_t)(lane / W) * bins + key[q0 + s];
+      old[s] = in[q0 + s] ? atomicOr(t + s * words + w, 1u << lane) : 1u;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      if (old[s] == 0u) {
+        uint32_t c;
+        if constexpr (kSplit) {
+          unsigned long long* pair = reinterpret_cast<unsigned long long*>(t + s * words + 2 * key[q0 + s]);
+          c = (uint32_t)__popcll(atomicExch(pair, 0ull));
+        } else {
+          c = (uint32_t)__popc(atomicExch(t + s * words + (uint32_t)(lane / W) * bins + key[q0 + s], 0u));
+        }
+        if (c) atomicAdd(my + key[q0 + s], c);
+      }
+    }
+    if constexpr (SPLIT) __syncwarp();
+  }
+}
+
 // ------------------------------------------------------------ staging layer
 // A warp chunk is ROWS rows of 32 consecutive 32-bit elements; after loading,
 // lane l holds row[r] = element base + 32 r + l (the paper's lane numbering:
@@ -406,6 +472,12 @@ __device__ __forceinline__ void mbar_init_fence() {
 // later async-proxy (TMA) writes to the same memory.
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// One arrival (release semantics at CTA scope: the arriving thread's earlier
+// writes, and those it has observed, are visible to a thread whose wait sees
+// the phase complete).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)

@@ -5,7 +5,9 @@
 // in arrival order while the arena and the slot count allow, packs all
 // admitted, not yet launched requests into one persistent launch on one of
 // kSlots streams (so a batch launched while an earlier one runs overlaps it
-// on the device), and marks requests done when their batch's event fires.
+// on the device), and marks each request done when the kernel raises the
+// request's flag in pinned host memory (after the request's last tile), or
+// at the latest when the batch's event fires.
 //
 // Device side.  A batch is a table of request descriptors; each request is
 // cut into tiles of kTile = 16384 elements (64 KB), numbered consecutively
@@ -55,34 +57,54 @@ struct ReqDesc {
 };
 
 struct BatchHdr {
-  unsigned long long next;
   int64_t nitems;
   int nreq;
-  int pad[11];
-};  // 64 bytes, followed by nreq ReqDesc, then nreq tile counters (zeroed by the host)
+  int pad[13];
+};  // 64 bytes, followed by nreq ReqDesc
 static_assert(sizeof(BatchHdr) == 64, "batch header layout");
 
-inline size_t table_bytes(size_t nreq) { return sizeof(BatchHdr) + nreq * (sizeof(ReqDesc) + sizeof(unsigned)); }
+inline size_t table_bytes(size_t nreq) { return sizeof(BatchHdr) + nreq * sizeof(ReqDesc); }
+
+// Batches of at most kParamReqs requests travel as a kernel parameter, so
+// their launch needs no copy of the table first.
+constexpr int kParamReqs = 24;
+struct ParamTable {
+  BatchHdr hdr;
+  ReqDesc reqs[kParamReqs];
+};
+
+// A slot's counters in device memory: the tile counter the CTAs take tiles
+// from, per request the tiles finished and the reduce tiles folded, and the
+// CTAs that have exited.  Zero before a launch; the launch's last CTA to
+// exit zeroes what the batch used, so the next launch on the slot (same
+// stream) finds them zero again.
+struct SlotCtr {
+  unsigned long long next;
+  unsigned exited;
+  unsigned pad;
+  unsigned fin[kMaxBatch];
+  unsigned red[kMaxBatch];
+};
 
 __host__ __device__ inline int64_t serve_items(int64_t n) { return (n + kTile - 1) / kTile; }
 
 // Dynamic shared memory of k_serve: the tile, the compaction's warp counts,
 // the mbarrier, and the per-request first-tile table.
-constexpr int kServeCounts = (int)(kTile / 512);
+constexpr int kServeCounts = kCompactWsWords;  // the compaction tile body's counts and offsets
 inline size_t serve_smem(size_t nreq) { return (size_t)(kTile + kServeCounts + 4) * 4 + nreq * 4; }
 
 // ---------------------------------------------------------------- reduce
-// Thread t folds elements 1024 j + 4 t + k (j = 0..15, k = 0..3) of the tile,
-// in that order; elements past the request's end were loaded as 0.
+// Thread t folds elements 1024 j + 4 t + k (j = 0..blocks-1, k = 0..3) of the
+// tile, in that order; elements past the request's end were loaded as 0.
 template <class R>
-__device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, const uint32_t* buf, typename R::V* wpart,
+__device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, const uint32_t* buf, int blocks, typename R::V* wpart,
                                   unsigned* ctr) {
   using T = typename R::T;
   using V = typename R::V;
   const int tid = threadIdx.x;
   V acc = R::ident();
 #pragma unroll 4
-  for (int j = 0; j < (int)(kTile / (4 * kServeBlock)); ++j) {
+  for (int j = 0; j < blocks; ++j) {  // (the rest of a partial tile would only add the identity)
     const uint4 q = *reinterpret_cast<const uint4*>(buf + j * 4 * kServeBlock + 4 * tid);
     acc = R::op(acc, R::load(from_bits<T>(q.x)));
     acc = R::op(acc, R::load(from_bits<T>(q.y)));
@@ -95,7 +117,7 @@ __device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, const uint32_t* b
   if (tid == 0) {
     part[c] = bsum;
     __threadfence();
-    s_last = atomicAdd(ctr, 1u) == (unsigned)(d.nitems - 1);
+    s_last = d.nitems == 1 || atomicAdd(ctr, 1u) == (unsigned)(d.nitems - 1);
   }
   __syncthreads();
   if (!s_last) return;
@@ -125,13 +147,14 @@ __device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, const uint32_t* b
 // bulk copy per request tile), so a lane's 16-byte reads of its row meet
 // 8-way bank conflicts; the tile's arithmetic, not shared memory, bounds it.
 template <class R, int W>
-__device__ void serve_scan_rows(uint32_t* buf) {
+__device__ void serve_scan_rows(uint32_t* buf, int rows) {
   using T = typename R::T;
   using V = typename R::V;
   uint4* b4 = reinterpret_cast<uint4*>(buf);
 #pragma unroll 1
   for (int h = 0; h < (int)(kTile / 32 / kServeBlock); ++h) {
     const int r = h * kServeBlock + threadIdx.x;
+    if (r >= rows) break;  // rows past a partial tile's end are not needed
     V v[32];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -150,32 +173,41 @@ __device__ void serve_scan_rows(uint32_t* buf) {
 }
 
 template <class R>
-__device__ void serve_scan_tile(const ReqDesc& d, uint32_t* buf) {
+__device__ void serve_scan_tile(const ReqDesc& d, uint32_t* buf, int rows) {
   switch (d.width) {
-    case 2: serve_scan_rows<R, 2>(buf); break;
-    case 4: serve_scan_rows<R, 4>(buf); break;
-    case 8: serve_scan_rows<R, 8>(buf); break;
-    case 16: serve_scan_rows<R, 16>(buf); break;
-    default: serve_scan_rows<R, 32>(buf); break;
+    case 2: serve_scan_rows<R, 2>(buf, rows); break;
+    case 4: serve_scan_rows<R, 4>(buf, rows); break;
+    case 8: serve_scan_rows<R, 8>(buf, rows); break;
+    case 16: serve_scan_rows<R, 16>(buf, rows); break;
+    default: serve_scan_rows<R, 32>(buf, rows); break;
   }
 }
 
-__global__ void __launch_bounds__(kServeBlock, 3) k_serve(uint8_t* table, uint32_t limit, unsigned* status) {
+// Marks a finished tile of request r (thread 0, after a __syncthreads that
+// follows the tile's last writes): the tile that completes the request
+// raises the request's flag in host memory, so the host sees each request
+// as soon as its own results are in memory, not when the whole launch ends.
+__device__ __forceinline__ void serve_tile_done(SlotCtr* ctr, unsigned* hflag, const ReqDesc* reqs, int r) {
+  __threadfence();
+  if (reqs[r].nitems == 1 || atomicAdd(ctr->fin + r, 1u) == (unsigned)(reqs[r].nitems - 1)) {
+    __threadfence_system();
+    asm volatile("st.release.sys.u32 [%0], %1;" ::"l"(hflag + r), "r"(1u) : "memory");
+  }
+}
+
+__device__ __forceinline__ void serve_body(const ReqDesc* reqs, int nreq, int64_t nitems, SlotCtr* ctr,
+                                           unsigned* hflag, uint32_t limit, unsigned* status) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ Pair wpart_c[32];
   __shared__ uint32_t wpart_u[32];
   __shared__ float wpart_f[32];
   __shared__ int64_t s_item;
   __shared__ int s_req;
+  __shared__ int s_last;
   uint32_t* buf = smem;                                           // the tile
   uint32_t* wcnt = smem + kTile;                                  // compaction warp counts
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kTile + kServeCounts);
   uint32_t* first = smem + kTile + kServeCounts + 4;              // first tile of every request
-  BatchHdr* hdr = reinterpret_cast<BatchHdr*>(table);
-  const ReqDesc* reqs = reinterpret_cast<const ReqDesc*>(table + sizeof(BatchHdr));
-  const int64_t nitems = hdr->nitems;
-  const int nreq = hdr->nreq;
-  unsigned* ctrs = reinterpret_cast<unsigned*>(table + sizeof(BatchHdr) + (size_t)nreq * sizeof(ReqDesc));
   const int tid = threadIdx.x;
   // Tile numbers fit 32 bits: a batch holds at most kMaxBatch requests of
   // fewer than 2^31 elements each.
@@ -185,14 +217,21 @@ __global__ void __launch_bounds__(kServeBlock, 3) k_serve(uint8_t* table, uint32
     mbar_init_fence();
   }
   uint32_t loads = 0;  // bulk copies completed on `bar`
+  int pending = -1;    // request of the tile this CTA finished last, not yet marked
   for (;;) {
     // Every thread's accesses to the tile, ordered before the async proxy's
-    // next write to it; the previous tile's bulk store has read the tile.
+    // next write to it; the previous tile's bulk store has completed.
     fence_proxy_async_smem();
-    if (tid == 0) tma_store_wait_read();
+    if (tid == 0) {
+      tma_store_wait_all();
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
     __syncthreads();
     if (tid == 0) {
-      const int64_t item = (int64_t)atomicAdd(&hdr->next, 1ull);
+      if (pending >= 0) serve_tile_done(ctr, hflag, reqs, pending);
+      // tiles come from the counter only: a tile is only ever handed to a CTA
+      // that runs, which a compaction tile's look-back relies on
+      const int64_t item = (int64_t)atomicAdd(&ctr->next, 1ull);
       s_item = item;
       if (item < nitems) {
         int lo = 0, hi = nreq;  // last request whose first tile <= item
@@ -204,6 +243,7 @@ __global__ void __launch_bounds__(kServeBlock, 3) k_serve(uint8_t* table, uint32
         s_req = lo;
       }
     }
+    pending = -1;
     __syncthreads();
     const int64_t item = s_item;
     if (item >= nitems) break;
@@ -227,22 +267,28 @@ __global__ void __launch_bounds__(kServeBlock, 3) k_serve(uint8_t* table, uint32
         break;
       }
     } else {
-      for (int i = tid; i < (int)kTile; i += blockDim.x) buf[i] = i < valid ? d.in[base + i] : 0u;
+      // a partial tile: its keys, then zeros up to the block (reduce: 1024
+      // elements) or row (scan: 32) that holds its end
+      const int span = d.kind == COX_REQ_REDUCE ? 1024 : d.kind == COX_REQ_SCAN ? 32 : 1;
+      const int end = (valid + span - 1) / span * span;
+      for (int i = tid; i < end; i += blockDim.x) buf[i] = i < valid ? d.in[base + i] : 0u;
       __syncthreads();
     }
     if (d.kind == COX_REQ_REDUCE) {
+      const int blocks = (valid + 1023) / 1024;
       if (d.dt == COX_F32) {
-        if (d.flags & COX_F_COMPENSATED) serve_reduce_tile<Comp>(d, c, buf, wpart_c, ctrs + s_req);
-        else serve_reduce_tile<Plain<AddF>>(d, c, buf, wpart_f, ctrs + s_req);
+        if (d.flags & COX_F_COMPENSATED) serve_reduce_tile<Comp>(d, c, buf, blocks, wpart_c, ctr->red + s_req);
+        else serve_reduce_tile<Plain<AddF>>(d, c, buf, blocks, wpart_f, ctr->red + s_req);
       } else {
-        serve_reduce_tile<Plain<AddU>>(d, c, buf, wpart_u, ctrs + s_req);
+        serve_reduce_tile<Plain<AddU>>(d, c, buf, blocks, wpart_u, ctr->red + s_req);
       }
     } else if (d.kind == COX_REQ_SCAN) {
+      const int rows = (valid + 31) / 32;
       if (d.dt == COX_F32) {
-        if (d.flags & COX_F_COMPENSATED) serve_scan_tile<Comp>(d, buf);
-        else serve_scan_tile<Plain<AddF>>(d, buf);
+        if (d.flags & COX_F_COMPENSATED) serve_scan_tile<Comp>(d, buf, rows);
+        else serve_scan_tile<Plain<AddF>>(d, buf, rows);
       } else {
-        serve_scan_tile<Plain<AddU>>(d, buf);
+        serve_scan_tile<Plain<AddU>>(d, buf, rows);
       }
       uint32_t* dst = d.out + base;
       if (valid == kTile && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
@@ -257,26 +303,72 @@ __global__ void __launch_bounds__(kServeBlock, 3) k_serve(uint8_t* table, uint32
       int64_t* count = reinterpret_cast<int64_t*>(d.ws);
       uint64_t* desc = reinterpret_cast<uint64_t*>(d.ws + kAlign);
       if (d.dt == COX_I32)
-        compact_big_tile<true>(buf, valid, d.threshold, d.out, count, desc, c, d.nitems, d.n, limit, status, wcnt);
+        compact_big_tile<true, kServeBlock / 32>(buf, valid, d.threshold, d.out, count, desc, c, d.nitems, d.n, limit,
+                                                 status, wcnt);
       else
-        compact_big_tile<false>(buf, valid, d.threshold, d.out, count, desc, c, d.nitems, d.n, limit, status,
-                                wcnt);
+        compact_big_tile<false, kServeBlock / 32>(buf, valid, d.threshold, d.out, count, desc, c, d.nitems, d.n, limit,
+                                                  status, wcnt);
+    }
+    pending = s_req;  // marked at the top of the next round, once its writes (and bulk store) are done
+  }
+  // ---- the last tile's mark; the last CTA out zeroes the slot's counters
+  fence_proxy_async_smem();
+  if (tid == 0) {
+    tma_store_wait_all();  // no bulk store outlives the CTA
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (pending >= 0) serve_tile_done(ctr, hflag, reqs, pending);
+    __threadfence();
+    s_last = atomicAdd(&ctr->exited, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    for (int r = tid; r < nreq; r += blockDim.x) {
+      ctr->fin[r] = 0u;
+      ctr->red[r] = 0u;
+    }
+    if (tid == 0) {
+      ctr->next = 0ull;
+      ctr->exited = 0u;
+    }
+    __syncthreads();
+    if (tid == 0) {  // the whole batch is done: the host may reuse the slot
+      __threadfence_system();
+      asm volatile("st.release.sys.u32 [%0], %1;" ::"l"(hflag + kMaxBatch), "r"(1u) : "memory");
     }
   }
-  if (tid == 0) tma_store_wait_all();  // no bulk store outlives the CTA
+}
+
+
+__global__ void __launch_bounds__(kServeBlock, 3) k_serve_tab(const uint8_t* __restrict__ table, SlotCtr* ctr,
+                                                              unsigned* hflag, uint32_t limit, unsigned* status) {
+  const BatchHdr* hdr = reinterpret_cast<const BatchHdr*>(table);
+  serve_body(reinterpret_cast<const ReqDesc*>(table + sizeof(BatchHdr)), hdr->nreq, hdr->nitems, ctr, hflag, limit,
+             status);
+}
+
+__global__ void __launch_bounds__(kServeBlock, 3) k_serve_par(const __grid_constant__ ParamTable pt, SlotCtr* ctr,
+                                                              unsigned* hflag, uint32_t limit, unsigned* status) {
+  serve_body(pt.reqs, pt.hdr.nreq, pt.hdr.nitems, ctr, hflag, limit, status);
 }
 
 // Zeroes the look-back descriptors of every compaction request of a batch
 // (launched only for batches that hold one).
-__global__ void k_serve_prep(const uint8_t* __restrict__ table) {
-  const BatchHdr* hdr = reinterpret_cast<const BatchHdr*>(table);
-  const ReqDesc* reqs = reinterpret_cast<const ReqDesc*>(table + sizeof(BatchHdr));
-  if ((int)blockIdx.x >= hdr->nreq) return;
-  const ReqDesc d = reqs[blockIdx.x];
+__device__ __forceinline__ void serve_prep(const ReqDesc& d) {
   if (d.kind != COX_REQ_COMPACT) return;
   const size_t words = compact_ws_bytes(d.nitems) / 4;  // count, tile and group descriptors
   uint32_t* w = reinterpret_cast<uint32_t*>(d.ws);
   for (size_t i = threadIdx.x; i < words; i += blockDim.x) w[i] = 0u;
+}
+__global__ void k_serve_prep_tab(const uint8_t* __restrict__ table) {
+  const BatchHdr* hdr = reinterpret_cast<const BatchHdr*>(table);
+  if ((int)blockIdx.x < hdr->nreq) serve_prep(reinterpret_cast<const ReqDesc*>(table + sizeof(BatchHdr))[blockIdx.x]);
+}
+__global__ void k_serve_prep_par(const __grid_constant__ ParamTable pt) {
+  if ((int)blockIdx.x < pt.hdr.nreq) serve_prep(pt.reqs[blockIdx.x]);
 }
 
 // --------------------------------------------------------------- host side
@@ -293,7 +385,10 @@ void request_bytes(const cox_request& r, size_t* out_b, size_t* ws_b) {
   switch (r.kind) {
     case COX_REQ_REDUCE: *out_b = kAlign; *ws_b = round_up((size_t)items * 8); break;
     case COX_REQ_SCAN: *out_b = round_up((size_t)r.n * 4); *ws_b = 0; break;
-    default: *out_b = round_up((size_t)r.n * 4); *ws_b = round_up(compact_ws_bytes(items)); break;
+    default:  // [count | descriptors]: the batch kernel's, or a solo cox_ballot_compact's workspace
+      *out_b = round_up((size_t)r.n * 4);
+      *ws_b = kAlign + round_up(std::max(compact_ws_bytes(items), cox_ballot_compact_workspace(r.n, 256)));
+      break;
   }
 }
 
@@ -359,21 +454,33 @@ struct SReq {
   cox_request r;
   ReqState state = kQueued;
   size_t off = 0, bytes = 0, out_b = 0, held = 0;
-  double t_ready = 0.0, t_done = 0.0;
+  double t_submit = 0.0, t_ready = 0.0, t_launch = 0.0, t_done = 0.0;
 };
 
-// While a batch runs, admitted requests wait for the next launch until they
-// fill the persistent grid with tiles or the oldest has waited this long:
-// fewer, larger batches under load, no added wait when the device is idle.
+// While two or more batches run, admitted requests wait for the next launch
+// until they fill the persistent grid with tiles or the oldest has waited
+// this long: fewer, larger batches under load, no added wait at low load.
 constexpr double kBatchDelay = 20e-6;
+constexpr double kEventPoll = 100e-6;  // how often a running batch's event is queried
 
 struct Slot {
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
   uint8_t* host_tab = nullptr;
   uint8_t* dev_tab = nullptr;
+  SlotCtr* ctr = nullptr;     // device counters, zero between launches
+  unsigned* hflag = nullptr;  // per request of the batch: 1 once its results are in memory; word kMaxBatch:
+                              // 1 once the whole batch is done (pinned, mapped)
+  unsigned* dflag = nullptr;  // the same flags' device address
   bool busy = false;
+  // Set once the batch's work and event are enqueued: until then the event
+  // still describes the slot's previous batch (the launch may run on another
+  // thread than the completion checks).
+  std::atomic<bool> issued{false};
+  bool solo = false;         // the batch ran as one op's own kernel (no flags: its event tells)
+  double t_checked = 0.0;    // when the slot's event was last queried
   std::vector<uint64_t> tickets;
+  std::vector<char> marked;  // requests of the batch already marked done
 };
 
 }  // namespace cox
@@ -393,6 +500,7 @@ struct cox_server {
   std::condition_variable cv;
   std::deque<uint64_t> queue;
   std::vector<uint64_t> ready;
+  int64_t ready_items = 0;  // tiles of the admitted, not yet launched requests
   std::unordered_map<uint64_t, SReq> reqs;
   std::vector<std::pair<uint64_t, double>> finished;  // (ticket, t_done) for trace runners
   bool collect_finished = false;
@@ -410,8 +518,10 @@ struct cox_server {
     ReqDesc* d = reinterpret_cast<ReqDesc*>(sl.host_tab + sizeof(BatchHdr));
     int64_t items = 0;
     bool compact = false;
+    const double t_launch = now_s();
     for (size_t i = 0; i < ts.size(); ++i) {
       SReq& q = reqs[ts[i]];
+      q.t_launch = t_launch;
       ReqDesc& e = d[i];
       e.kind = q.r.kind;
       e.dt = q.r.dt;
@@ -429,11 +539,14 @@ struct cox_server {
       q.state = kRunning;
     }
     // (requests are < 2^31 elements each, so 2048 of them stay < 2^31 tiles)
-    std::memset(sl.host_tab + sizeof(BatchHdr) + ts.size() * sizeof(ReqDesc), 0, ts.size() * sizeof(unsigned));
-    h->next = 0;
     h->nitems = items;
     h->nreq = (int)ts.size();
+    for (size_t i = 0; i < ts.size(); ++i) __atomic_store_n(sl.hflag + i, 0u, __ATOMIC_RELAXED);
+    __atomic_store_n(sl.hflag + kMaxBatch, 0u, __ATOMIC_RELAXED);
+    sl.t_checked = 0.0;
     sl.tickets = ts;
+    sl.marked.assign(ts.size(), 0);
+    sl.issued.store(false, std::memory_order_relaxed);
     sl.busy = true;
     stats.batches += 1;
     stats.max_batch = std::max<int64_t>(stats.max_batch, (int64_t)ts.size());
@@ -444,21 +557,120 @@ struct cox_server {
 
   // Enqueues a filled batch on the slot's stream (without `mu`: submitters
   // are not held up by the launch calls).
+  // A batch of one scan or compaction runs the op's own kernel (cox_tile_scan,
+  // cox_ballot_compact): the same results bit for bit, at the latency of one
+  // launch per request.  Other small batches pass their table as a kernel
+  // parameter; larger ones copy it to the slot's device table first.
   bool issue_batch(Slot& sl, size_t tab_bytes, int64_t items, bool has_compact) {
-    bool ok = cudaMemcpyAsync(sl.dev_tab, sl.host_tab, tab_bytes, cudaMemcpyHostToDevice, sl.st) == cudaSuccess;
-    if (ok) {
-      const int nreq = reinterpret_cast<BatchHdr*>(sl.host_tab)->nreq;
-      if (has_compact) k_serve_prep<<<(unsigned)nreq, 256, 0, sl.st>>>(sl.dev_tab);
-      const int g = (int)std::min<int64_t>(grid, items);
-      k_serve<<<g, kServeBlock, serve_smem((size_t)nreq), sl.st>>>(sl.dev_tab, spin_limit(), device_status_word());
-      ok = cudaGetLastError() == cudaSuccess && cudaEventRecord(sl.ev, sl.st) == cudaSuccess;
+    const int nreq = reinterpret_cast<BatchHdr*>(sl.host_tab)->nreq;
+    if (nreq == 1) {
+      const ReqDesc& d = *reinterpret_cast<const ReqDesc*>(sl.host_tab + sizeof(BatchHdr));
+      cox_status c = COX_EINVAL;
+      if (d.kind == COX_REQ_SCAN) {
+        c = cox_tile_scan(COX_SUM, (cox_dtype)d.dt, d.width, 256, d.in, d.out, d.n, d.flags, sl.st);
+      } else if (d.kind == COX_REQ_COMPACT) {
+        const size_t wsb = cox_ballot_compact_workspace(d.n, 256);
+        c = cox_ballot_compact((cox_dtype)d.dt, 32, 256, d.in, d.n, d.threshold, d.out,
+                               reinterpret_cast<int64_t*>(d.ws), d.ws + kAlign, wsb, 0u, sl.st);
+      }
+      if (d.kind != COX_REQ_REDUCE) {
+        sl.solo = true;
+        return c == COX_OK && cudaEventRecord(sl.ev, sl.st) == cudaSuccess;
+      }
     }
-    return ok;
+    sl.solo = false;
+    has_compact = has_compact && items > 1;  // (a lone tile's look-back reads no descriptor)
+    const int g = (int)std::min<int64_t>(grid, items);
+    const size_t smem = serve_smem((size_t)nreq);
+    if (nreq <= kParamReqs) {
+      ParamTable pt;
+      std::memcpy(&pt.hdr, sl.host_tab, sizeof(BatchHdr));
+      std::memcpy(pt.reqs, sl.host_tab + sizeof(BatchHdr), (size_t)nreq * sizeof(ReqDesc));
+      if (has_compact) k_serve_prep_par<<<(unsigned)nreq, 256, 0, sl.st>>>(pt);
+      k_serve_par<<<g, kServeBlock, smem, sl.st>>>(pt, sl.ctr, sl.dflag, spin_limit(), device_status_word());
+    } else {
+      if (cudaMemcpyAsync(sl.dev_tab, sl.host_tab, tab_bytes, cudaMemcpyHostToDevice, sl.st) != cudaSuccess)
+        return false;
+      if (has_compact) k_serve_prep_tab<<<(unsigned)nreq, 256, 0, sl.st>>>(sl.dev_tab);
+      k_serve_tab<<<g, kServeBlock, smem, sl.st>>>(sl.dev_tab, sl.ctr, sl.dflag, spin_limit(), device_status_word());
+    }
+    return cudaGetLastError() == cudaSuccess && cudaEventRecord(sl.ev, sl.st) == cudaSuccess;
+  }
+
+  // Marks request i of a running batch done (caller holds `mu`).
+  void mark_done(Slot& sl, size_t i, ReqState state, double t) {
+    if (sl.marked[i]) return;
+    sl.marked[i] = 1;
+    auto it = reqs.find(sl.tickets[i]);
+    if (it == reqs.end()) return;
+    it->second.state = state;
+    it->second.t_done = t;
+    if (collect_finished) finished.emplace_back(sl.tickets[i], t);
+    if (state == kDone) {
+      stats.completed += 1;
+      stats.wait_s += it->second.t_launch - it->second.t_submit;
+      stats.run_s += t - it->second.t_launch;
+    } else {
+      stats.failed += 1;
+    }
+  }
+
+  // Admits queued requests in arrival order while the budget and the slot
+  // count allow, then picks a free slot for the admitted ones when the rule
+  // below says go (caller holds `mu`).  Returns the slot to launch, or null.
+  Slot* plan_launch(size_t* tab_bytes, int64_t* items, bool* has_compact) {
+    const double now = now_s();
+    while (!queue.empty() && admitted < max_req) {
+      SReq& q = reqs[queue.front()];
+      size_t off;
+      if (used + q.held > budget || !arena->alloc(q.bytes, &off)) break;
+      q.off = off;
+      q.state = kReady;
+      q.t_ready = now;
+      used += q.held;
+      peak = std::max(peak, used);
+      ++admitted;
+      ready_items += serve_items(q.r.n);
+      ready.push_back(queue.front());
+      queue.pop_front();
+    }
+    int inflight = 0;
+    for (const Slot& sl : slots) inflight += sl.busy;
+    // Launch at once while at most one batch runs; with more in flight, hold
+    // the admitted requests back until they fill the grid or the oldest has
+    // waited kBatchDelay: fewer, larger batches under load.
+    const bool go = !ready.empty() && inflight < kSlots &&
+                    (inflight <= 1 || ready_items >= grid || now - reqs[ready.front()].t_ready >= kBatchDelay);
+    if (!go) return nullptr;
+    for (Slot& sl : slots) {
+      if (sl.busy) continue;
+      const size_t k = std::min<size_t>(ready.size(), kMaxBatch);
+      std::vector<uint64_t> ts(ready.begin(), ready.begin() + k);
+      ready.erase(ready.begin(), ready.begin() + k);
+      *tab_bytes = fill_batch(sl, ts, items, has_compact);
+      ready_items -= *items;
+      return &sl;
+    }
+    return nullptr;
+  }
+
+  // Enqueues a planned batch (without `mu`); on failure its requests fail.
+  void launch_planned(Slot* sl, size_t tab_bytes, int64_t items, bool has_compact) {
+    if (issue_batch(*sl, tab_bytes, items, has_compact)) {
+      sl->issued.store(true, std::memory_order_release);
+      return;
+    }
+    // What did get enqueued ends before the slot's table is written again.
+    cudaStreamSynchronize(sl->st);
+    std::lock_guard<std::mutex> g(mu);
+    for (size_t i = 0; i < sl->tickets.size(); ++i) mark_done(*sl, i, kFailed, now_s());
+    sl->tickets.clear();
+    sl->busy = false;
+    cv.notify_all();
   }
 
   void loop() {
     cudaSetDevice(dev);
-    int64_t ready_items = 0;  // tiles of the admitted, not yet launched requests
     while (!stop.load(std::memory_order_relaxed)) {
       bool progress = false;
       Slot* launch = nullptr;
@@ -467,74 +679,46 @@ struct cox_server {
       bool has_compact = false;
       {
         std::lock_guard<std::mutex> g(mu);
-        int inflight = 0;
-        for (Slot& sl : slots) {  // completions
-          if (!sl.busy) continue;
-          const cudaError_t e = cudaEventQuery(sl.ev);
-          if (e == cudaErrorNotReady) {
-            ++inflight;
-            continue;
-          }
+        // Completions, from the flags the batch kernel raises in host memory:
+        // each request's, then the batch's; its event is queried only now and
+        // then (every kEventPoll seconds), for a batch whose kernel failed.  A
+        // lone request run as its op's own kernel completes with its event.
+        for (Slot& sl : slots) {
+          if (!sl.busy || !sl.issued.load(std::memory_order_acquire)) continue;
           const double t = now_s();
-          for (uint64_t tk : sl.tickets) {
-            auto it = reqs.find(tk);
-            if (it == reqs.end()) continue;
-            it->second.state = e == cudaSuccess ? kDone : kFailed;
-            it->second.t_done = t;
-            if (collect_finished) finished.emplace_back(tk, t);
+          bool any = false;
+          for (size_t i = 0; i < sl.tickets.size(); ++i)
+            if (!sl.marked[i] && __atomic_load_n(sl.hflag + i, __ATOMIC_ACQUIRE)) {
+              mark_done(sl, i, kDone, t);
+              any = true;
+            }
+          bool free_slot = false;
+          ReqState rest = kDone;
+          if (__atomic_load_n(sl.hflag + kMaxBatch, __ATOMIC_ACQUIRE)) {
+            free_slot = true;
+          } else if (sl.solo || t - sl.t_checked >= kEventPoll) {
+            sl.t_checked = t;
+            const cudaError_t e = cudaEventQuery(sl.ev);
+            if (e != cudaErrorNotReady) {
+              free_slot = true;
+              rest = e == cudaSuccess ? kDone : kFailed;
+            }
           }
-          if (e == cudaSuccess) stats.completed += (int64_t)sl.tickets.size();
-          else stats.failed += (int64_t)sl.tickets.size();
-          sl.busy = false;
-          sl.tickets.clear();
-          progress = true;
-          cv.notify_all();
-        }
-        const double now = now_s();
-        while (!queue.empty() && admitted < max_req) {  // admission, in arrival order
-          SReq& q = reqs[queue.front()];
-          size_t off;
-          if (used + q.held > budget || !arena->alloc(q.bytes, &off)) break;
-          q.off = off;
-          q.state = kReady;
-          q.t_ready = now;
-          used += q.held;
-          peak = std::max(peak, used);
-          ++admitted;
-          ready_items += serve_items(q.r.n);
-          ready.push_back(queue.front());
-          queue.pop_front();
-          progress = true;
-        }
-        const bool go = !ready.empty() && inflight < kSlots &&
-                        (inflight == 0 || ready_items >= grid || now - reqs[ready.front()].t_ready >= kBatchDelay);
-        if (go) {
-          for (Slot& sl : slots) {
-            if (sl.busy) continue;
-            const size_t k = std::min<size_t>(ready.size(), kMaxBatch);
-            std::vector<uint64_t> ts(ready.begin(), ready.begin() + k);
-            ready.erase(ready.begin(), ready.begin() + k);
-            tab_bytes = fill_batch(sl, ts, &items, &has_compact);
-            ready_items -= items;
-            launch = &sl;
-            break;
+          if (free_slot) {
+            for (size_t i = 0; i < sl.tickets.size(); ++i) mark_done(sl, i, rest, t);
+            sl.busy = false;
+            sl.tickets.clear();
+          }
+          if (any || free_slot) {
+            progress = true;
+            cv.notify_all();
           }
         }
+        const size_t queued = queue.size();
+        launch = plan_launch(&tab_bytes, &items, &has_compact);
+        progress = progress || launch || queue.size() != queued;
       }
-      if (launch) {
-        progress = true;
-        if (!issue_batch(*launch, tab_bytes, items, has_compact)) {
-          // The batch's requests fail.  What did get enqueued ends before the
-          // slot's table is written again.
-          cudaStreamSynchronize(launch->st);
-          std::lock_guard<std::mutex> g(mu);
-          for (uint64_t t : launch->tickets) reqs[t].state = kFailed;
-          stats.failed += (int64_t)launch->tickets.size();
-          launch->tickets.clear();
-          launch->busy = false;
-          cv.notify_all();
-        }
-      }
+      if (launch) launch_planned(launch, tab_bytes, items, has_compact);
       if (!progress) std::this_thread::yield();
     }
   }
@@ -560,18 +744,24 @@ extern "C" cox_status cox_server_create(size_t budget_bytes, int max_requests, c
   for (Slot& sl : s->slots) {
     if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMallocHost(&sl.host_tab, tab) != cudaSuccess || cudaMalloc(&sl.dev_tab, tab) != cudaSuccess) {
+        cudaMallocHost(&sl.host_tab, tab) != cudaSuccess || cudaMalloc(&sl.dev_tab, tab) != cudaSuccess ||
+        cudaMalloc(&sl.ctr, sizeof(SlotCtr)) != cudaSuccess || cudaMemset(sl.ctr, 0, sizeof(SlotCtr)) != cudaSuccess ||
+        cudaHostAlloc(&sl.hflag, (kMaxBatch + 1) * sizeof(unsigned), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&sl.dflag, sl.hflag, 0) != cudaSuccess) {
       cox_server_destroy(s);
       return COX_ECUDA;
     }
   }
   const size_t smem = serve_smem(kMaxBatch);
-  if (cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  if (cudaFuncSetAttribute(k_serve_tab, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_serve_par, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {  // (the counters' zeroing has landed)
     cox_server_destroy(s);
     return COX_ECUDA;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve, kServeBlock, smem) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve_tab, kServeBlock, smem) != cudaSuccess ||
+      per_sm < 1)
     per_sm = 1;
   s->grid = per_sm * sm_count();
   device_status_word();
@@ -587,18 +777,33 @@ extern "C" cox_status cox_server_submit(cox_server* s, const cox_request* req, u
   if (c != COX_OK) return c;
   SReq q;
   q.r = *req;
+  q.t_submit = now_s();
   size_t ob, wb;
   request_bytes(*req, &ob, &wb);
   q.out_b = ob;
   q.bytes = ob + wb;
   q.held = q.bytes + round_up((size_t)req->n * 4);  // input counted as held while in flight
   if (q.bytes > s->budget || q.held > s->budget) return COX_ENOMEM;
-  std::lock_guard<std::mutex> g(s->mu);
-  const uint64_t t = s->next_ticket++;
-  s->reqs.emplace(t, q);
-  s->queue.push_back(t);
-  s->stats.submitted += 1;
-  *ticket = t;
+  Slot* launch = nullptr;
+  size_t tab_bytes = 0;
+  int64_t items = 0;
+  bool has_compact = false;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    const uint64_t t = s->next_ticket++;
+    s->reqs.emplace(t, q);
+    s->queue.push_back(t);
+    s->stats.submitted += 1;
+    *ticket = t;
+    // An idle server launches from the submitting thread (when the server's
+    // device is current there), without waiting for the scheduler thread to
+    // notice the request.
+    int cur = -1;
+    bool idle = s->queue.size() == 1 && s->ready.empty() && cudaGetDevice(&cur) == cudaSuccess && cur == s->dev;
+    for (const Slot& sl : s->slots) idle = idle && !sl.busy;
+    if (idle) launch = s->plan_launch(&tab_bytes, &items, &has_compact);
+  }
+  if (launch) s->launch_planned(launch, tab_bytes, items, has_compact);
   return COX_OK;
 }
 
@@ -693,6 +898,8 @@ extern "C" void cox_server_destroy(cox_server* s) {
     if (sl.st) cudaStreamDestroy(sl.st);
     if (sl.host_tab) cudaFreeHost(sl.host_tab);
     if (sl.dev_tab) cudaFree(sl.dev_tab);
+    if (sl.ctr) cudaFree(sl.ctr);
+    if (sl.hflag) cudaFreeHost(sl.hflag);
   }
   if (s->arena_mem) cudaFree(s->arena_mem);
   delete s->arena;

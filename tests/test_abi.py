@@ -52,7 +52,7 @@ def test_status_strings_and_version(cox):
 def test_workspace_sizes(cox):
     assert cox.cox_tile_reduce_workspace(cox.COX_SCOPE_TILE, 10**6, 256) == 0
     assert cox.cox_tile_reduce_workspace(cox.COX_SCOPE_GRID, 10**6, 256) > 0
-    tile = 16384
+    tile = 8192
     # header + a descriptor per tile + a descriptor and an accumulator per group of 32 tiles
     t = 2**28 // tile
     assert cox.cox_ballot_compact_workspace(2**28, 256) == 256 + 8 * t + 16 * ((t + 31) // 32)

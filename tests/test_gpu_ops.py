@@ -402,15 +402,16 @@ def test_compaction_unsigned_negative_keys_and_unaligned(cox):
 
 
 def test_compaction_lookback_timeout_is_reported(cox):
-    # The workspace says tile 0 was handed out already (ticket = 1) but its
-    # descriptor is never published: tile 1's look-back must give up after the
-    # spin limit, record COX_ETIMEOUT, and every CTA must still finish.
+    # Tile 0's descriptor is withheld in the caller-zeroed workspace (both
+    # flag bits set: descriptors only grow, so tile 0's publish cannot clear
+    # it): tile 1's look-back must give up after the spin limit, record
+    # COX_ETIMEOUT, and every CTA must still finish.
     import torch
-    n = 16384 * 8
+    n = 8192 * 8
     k = dev(inputs.uniform_u31(n, seed=1))
     ws_bytes = cox.cox_ballot_compact_workspace(n, 256)
-    ws = torch.zeros(ws_bytes // 4, dtype=torch.int32, device="cuda")
-    ws[0] = 1
+    ws = torch.zeros(ws_bytes // 8, dtype=torch.int64, device="cuda")
+    ws[256 // 8] = -(1 << 62)  # 0xC000000000000000: tile 0's descriptor, withheld
     out = torch.empty(n, dtype=torch.int32, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     cox.cox_set_spin_limit(1000)
@@ -425,6 +426,7 @@ def test_compaction_lookback_timeout_is_reported(cox):
     got, c = cox.ballot_compact(k, 2**30)  # and the library still works
     want, wc = o.ballot_compact(o.I32, 32, 256, host(k), 2**30)
     assert int(c.item()) == wc
+    np.testing.assert_array_equal(host(got)[:wc], want)
 
 
 # ----------------------------------------------------- cox_match_histogram

@@ -143,6 +143,27 @@ def test_full_size_mix_against_the_oracle(cox):
     assert cox.device_status() == cox.COX_OK
 
 
+def test_requests_one_at_a_time_match_the_oracle(cox):
+    """An idle server launches each request from the submitting thread (a lone
+    scan or compaction with the op's own kernel); a request must not be marked
+    done before its results are in memory, so every result read right after
+    the wait must match the oracle."""
+    mix = make_mix(cox, 36, seed=51, lo=1000, hi=1 << 20)
+    srv = cox.Server(1 << 30)
+    try:
+        for r, d, h in mix:
+            t = srv.submit(r, keep=d)
+            srv.wait(t)
+            got = srv.result(t, r)
+            srv.release(t)
+            check_against_oracle(cox, r, h, got)
+        st = srv.stats()
+        assert st["completed"] == len(mix) and st["failed"] == 0 and st["used_bytes"] == 0
+    finally:
+        srv.close()
+    assert cox.device_status() == cox.COX_OK
+
+
 def test_admission_respects_the_budget(cox):
     import torch
     budget = 8 << 20

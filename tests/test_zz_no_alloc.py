@@ -81,8 +81,8 @@ def test_input_beyond_the_fixed_scratch_is_refused(cox):
     keys = torch.zeros(16, dtype=torch.int32, device="cuda")
     out = torch.zeros(16, dtype=torch.int32, device="cuda")
     cnt = torch.full((1,), -1, dtype=torch.int64, device="cuda")  # a sentinel no run of the kernel leaves
-    # 256 header bytes + 8 per tile of 16384 keys + 16 per group of 32 tiles: at most 123330 tiles
-    limit = 123330 * 16384
+    # 256 header bytes + 8 per tile of 8192 keys + 16 per group of 32 tiles: at most 123330 tiles
+    limit = 123330 * 8192
     assert cox.cox_ballot_compact_workspace(limit, 256) <= cox.COX_COMPACT_STATIC_SCRATCH_BYTES
     assert cox.cox_ballot_compact_workspace(limit + 1, 256) > cox.COX_COMPACT_STATIC_SCRATCH_BYTES
     st = cox.cox_ballot_compact_static(cox.COX_I32, 32, 256, keys.data_ptr(), limit + 1, 0, out.data_ptr(),
