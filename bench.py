@@ -351,13 +351,44 @@ def run_secondary(dev, st):
     # block sum, 64 blocks x 256 threads of int32 (launch-latency bound)
     x = torch.from_numpy(inputs.uniform_int32(16384, -1000, 1000, inputs.BASE_SEED)).to(dev)
     out = torch.empty(64, dtype=torch.int32, device=dev)
-    ms = _time_launches(st, lambda: chk(cox.cox_tile_reduce(0, 0, 32, 256, 1, x.data_ptr(), out.data_ptr(), 16384, 0,
-                                                            None, None, 0, sh)), iters=200)
-    res["block_sum_64x256_int32"] = {"us_per_call": round(ms * 1e3, 2)}
+    block_sum = lambda s: chk(cox.cox_tile_reduce(0, 0, 32, 256, 1, x.data_ptr(), out.data_ptr(), 16384, 0, None,
+                                                  None, 0, s))
+    ms = _time_launches(st, lambda: block_sum(sh), iters=200)
+    # the same call 100 times inside one captured CUDA graph (launch overhead amortised by the graph)
+    gs = torch.cuda.Stream(device=dev)
+    for _ in range(3):
+        block_sum(gs.cuda_stream)
+    gs.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gs):
+        for _ in range(100):
+            block_sum(gs.cuda_stream)
+    with torch.cuda.stream(gs):  # (replay launches on the current stream)
+        ms_graph = _time_launches(gs, graph.replay, iters=20) / 100
+    del graph
+    res["block_sum_64x256_int32"] = {"us_per_call": round(ms * 1e3, 2), "us_per_call_in_graph": round(ms_graph * 1e3, 3),
+                                     "GB/s_in_graph": round((16384 * 4 + 64 * 4) / (ms_graph * 1e-3) / 1e9, 1),
+                                     "graph": "100 calls captured once, replayed"}
 
-    # tile reduce of 2^26 fp32 (one result per tile; compensated with its low word)
+    # the headline scans in their shuffle form: the same 2^26 elements starting 4 bytes
+    # past a 16-byte boundary take the one-element-per-lane shfl_up kernel
     n = 1 << 26
     f = torch.from_numpy(inputs.normal_f32(n, inputs.BASE_SEED + 1)).to(dev)
+    f1 = torch.empty(n + 4, dtype=torch.float32, device=dev)
+    f1[1:n + 1] = f
+    y1 = torch.empty(n + 4, dtype=torch.float32, device=dev)
+    sf = {}
+    for w, comp in VARIANTS:
+        ms = _time_launches(st, lambda: chk(cox.cox_tile_scan(0, 2, w, BLOCK, f1.data_ptr() + 4, y1.data_ptr() + 4, n,
+                                                              1 if comp else 0, sh)))
+        gbs = n * 8 / (ms * 1e-3) / 1e9
+        sf[f"W{w}{'_comp' if comp else '_plain'}"] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1),
+                                                     "frac": round(gbs / peak, 3)}
+    sf["note"] = "input and output 4 bytes past a 16-byte boundary: k_tile_scan (shfl_up per lane), not the rows kernel"
+    res["tile_scan_2p26_fp32_shuffle_form"] = sf
+    del f1, y1
+
+    # tile reduce of 2^26 fp32 (one result per tile; compensated with its low word)
     tr = {}
     for W in (2, 32):
         y = torch.empty(n // W, dtype=torch.float32, device=dev)
@@ -579,44 +610,45 @@ def run_batched(dev, st, num_arrays=10_000):
     finally:
         cox.cox_graph_destroy(graph)
     # the same batch without peer groups (one shared atomic per key), for comparison
-    direct = cox.cox_batch_tune(best.block_dim, best.ctas_per_sm, best.width, best.fp64_segments, 2)
+    direct = cox.cox_batch_tune(best.block_dim, best.ctas_per_sm, best.width, best.fp64_segments, 2, best.ept)
     ms_direct = _time_launches(st, lambda: chk(cox.cox_batch_sum_hist(
         num_arrays, pv.data_ptr(), pk.data_ptr(), ctypes.addressof(direct), ws.data_ptr(), wsb, sums.data_ptr(),
         sums64.data_ptr(), hists.data_ptr(), sh)), iters=10)
     nbytes = E * 8
     peak, _ = _peaks()
 
-    # one launch per array: grid-scope compensated sum + match histogram
-    rws_b = cox.cox_tile_reduce_workspace(2, 1 << 20, 256)
-    rws = torch.empty(rws_b, dtype=torch.uint8, device=dev)
-    ign = torch.empty(1, dtype=torch.int64, device=dev)
-    vp, kp = vals.data_ptr(), keys.data_ptr()
-    s_p, h_p = sums.data_ptr(), hists.data_ptr()
+    # one launch per array: grid-scope compensated sum + match histogram, launched
+    # from a C loop (cox_batch_percall), an event recorded after each array
+    h_vals = (ctypes.c_void_p * num_arrays)(*[vals.data_ptr() + 4 * int(o) for o in starts])
+    h_keys = (ctypes.c_void_p * num_arrays)(*[keys.data_ptr() + 4 * int(o) for o in starts])
+    h_lens = lens.astype(np.int64)
+    pscr_b = cox.cox_batch_percall_scratch(int(lens.max()))
+    pscr = torch.empty(pscr_b, dtype=torch.uint8, device=dev)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(num_arrays)]
+    for e in evs:  # (torch creates the CUDA event at its first record)
+        e.record(st)
+    h_ev = (ctypes.c_void_p * num_arrays)(*[e.cuda_event for e in evs])
 
     def per_call(events=None):
-        for a in range(num_arrays):
-            L, o4 = int(lens[a]), 4 * int(starts[a])
-            chk(cox.cox_tile_reduce(0, 2, 32, 256, 2, vp + o4, s_p + 4 * a, L, 1, None, rws.data_ptr(), rws_b, sh))
-            chk(cox.cox_match_histogram(0, 32, 256, kp + o4, L, 256, h_p + 1024 * a, ign.data_ptr(), 0, sh))
-            if events is not None:
-                events[a].record(st)
+        chk(cox.cox_batch_percall(num_arrays, h_vals, h_keys, h_lens.ctypes.data, sums.data_ptr(), hists.data_ptr(),
+                                  pscr.data_ptr(), pscr_b, events, sh), "cox_batch_percall")
 
     per_call()  # warm-up
     st.synchronize()
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(num_arrays)]
     t0 = torch.cuda.Event(enable_timing=True)
     t0.record(st)
-    per_call(evs)
+    per_call(h_ev)
     evs[-1].synchronize()
     done = np.array([t0.elapsed_time(e) for e in evs])
     pc_ms = float(done[-1])
     return {"arrays": num_arrays, "elements": E, "bytes": nbytes,
-            "tune": dict(zip(["block_dim", "ctas_per_sm", "width", "fp64_segments", "native_match"], best.astuple())),
+            "tune": dict(zip(["block_dim", "ctas_per_sm", "width", "fp64_segments", "native_match", "ept"],
+                             best.astuple())),
             "graph_ms": round(ms, 4), "GB/s": round(nbytes / (ms * 1e-3) / 1e9, 1),
             "frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 3),
             "latency_ms": {"p50": round(ms, 4), "p99": round(ms, 4), "note": "every array completes with the batch"},
             "per_call": {"ms": round(pc_ms, 3), "GB/s": round(nbytes / (pc_ms * 1e-3) / 1e9, 1),
-                         "launches": 2 * num_arrays,
+                         "launches": 2 * num_arrays, "how": "cox_batch_percall: a C loop, one stream",
                          "latency_ms": {"p50": round(float(np.percentile(done, 50)), 3),
                                         "p99": round(float(np.percentile(done, 99)), 3)}},
             "speedup_vs_per_call": round(pc_ms / ms, 2),

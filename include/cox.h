@@ -391,7 +391,7 @@ cox_status cox_match_histogram(cox_dtype dt, int width, int block_dim, const voi
 /* ====================================================================== */
 
 /* Launch shape of the batched kernel.  Every field must be set (or pass a
- * NULL tune to take the library default, {512, 2, 32, 8, 3}). */
+ * NULL tune to take the library default, {512, 2, 32, 8, 3, 8}). */
 typedef struct {
   int block_dim;     /* threads per CTA, multiple of 32 in [64, 1024] */
   int ctas_per_sm;   /* persistent CTAs per SM, 1..8 */
@@ -404,6 +404,8 @@ typedef struct {
                         word in their tile's copy of the table; the lane that found the word
                         empty takes the mask and clears it), or from the ballots of 0 where
                         that table (2 x 32 / width x 1 KB per warp) does not fit an SM */
+  int ept;           /* elements per thread per round: 4, 8 or 16 (128-bit loads in flight per
+                        thread: ept / 4); the fold order, and so every result, is the same for all */
 } cox_batch_tune;
 
 /* Bytes of device workspace for a batch of num_arrays arrays (any tune). */
@@ -439,6 +441,22 @@ cox_status cox_batch_sum_hist(int64_t num_arrays, const float* const* d_vals, co
                               const cox_batch_tune* tune, void* d_workspace, size_t workspace_bytes,
                               float* d_sums, double* d_sums64, int32_t* d_hists, void* stream);
 
+/*
+ * cox_batch_percall -- the batch's results the slow way, for comparison: one
+ * compensated GRID-scope cox_tile_reduce and one cox_match_histogram (width
+ * 32) per array, launched back to back from a C loop on `stream`.  h_vals /
+ * h_keys: HOST arrays of the arrays' device pointers; h_lens: host lengths.
+ * d_sums / d_hists as cox_batch_sum_hist (d_sums from a different order of
+ * additions: within the same tolerance, not the same bits).  d_scratch:
+ * cox_batch_percall_scratch(longest length) bytes, 16-byte aligned.
+ * events: optional host array of num_arrays cudaEvent_t (entries may be
+ * NULL), each recorded after its array's launches.
+ */
+size_t cox_batch_percall_scratch(int64_t max_len);
+cox_status cox_batch_percall(int64_t num_arrays, const float* const* h_vals, const int32_t* const* h_keys,
+                             const int64_t* h_lens, float* d_sums, int32_t* d_hists, void* d_scratch,
+                             size_t scratch_bytes, void* const* events, void* stream);
+
 /* An instantiated CUDA graph of one cox_batch_sum_hist call. */
 typedef struct cox_graph cox_graph;
 
@@ -452,11 +470,13 @@ void cox_graph_destroy(cox_graph* g);
 
 /*
  * cox_batch_autotune -- times every candidate tune (block_dim 256/512/1024 x
- * ctas_per_sm 1/2/4 x width 8/32, ballot-built peer masks) on this batch (prepared in d_workspace)
- * with CUDA events, `reps` timed runs each, and returns the fastest in *best
- * (and its mean milliseconds in *best_ms if non-NULL).  If cache_path is not
- * NULL the winner is appended to that file as one line
- * "<gpu name>|batch_sum_hist|<arrays bucket>|<elements bucket>|b,c,w,f,m|ms".
+ * ctas_per_sm 1/2/4 x width 8/32 x elements per thread 4/8/16; fp64_segments
+ * 8 and the table-built peer masks, native_match 3, in every candidate) on
+ * this batch (prepared in d_workspace) with CUDA events, `reps` timed runs
+ * each, and returns the fastest in *best (and its mean milliseconds in
+ * *best_ms if non-NULL).  If cache_path is not NULL the winner is appended to
+ * that file as one line
+ * "<gpu name>|batch_sum_hist|<arrays bucket>|<elements bucket>|b,c,w,f,m,e|ms".
  * Synchronises `stream`.  Overwrites the output buffers.
  */
 cox_status cox_batch_autotune(int64_t num_arrays, const float* const* d_vals, const int32_t* const* d_keys,

@@ -59,6 +59,8 @@ SIGNATURES = {
     "cox_batch_workspace": (_SZ, [_I64]),
     "cox_batch_prepare": (_I, [_I64, _P, _P, _SZ, _P]),
     "cox_batch_sum_hist": (_I, [_I64, _P, _P, _P, _P, _SZ, _P, _P, _P, _P]),
+    "cox_batch_percall_scratch": (_SZ, [_I64]),
+    "cox_batch_percall": (_I, [_I64, _P, _P, _P, _P, _P, _P, _SZ, _P, _P]),
     "cox_batch_graph_create": (_I, [_I64, _P, _P, _P, _P, _SZ, _P, _P, _P, _P]),
     "cox_graph_launch": (_I, [_P, _P]),
     "cox_graph_destroy": (None, [_P]),
@@ -188,12 +190,15 @@ def cox_match_histogram(dt, width, block_dim, d_keys, n, bins, d_hist, d_ignored
 
 
 class cox_batch_tune(ctypes.Structure):
-    """Launch shape of the batched kernel (mirrors the C struct)."""
+    """Launch shape of the batched kernel (mirrors the C struct; ept defaults to 8)."""
     _fields_ = [("block_dim", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("width", ctypes.c_int),
-                ("fp64_segments", ctypes.c_int), ("native_match", ctypes.c_int)]
+                ("fp64_segments", ctypes.c_int), ("native_match", ctypes.c_int), ("ept", ctypes.c_int)]
+
+    def __init__(self, block_dim=0, ctas_per_sm=0, width=0, fp64_segments=0, native_match=0, ept=8):
+        super().__init__(block_dim, ctas_per_sm, width, fp64_segments, native_match, ept)
 
     def astuple(self):
-        return (self.block_dim, self.ctas_per_sm, self.width, self.fp64_segments, self.native_match)
+        return (self.block_dim, self.ctas_per_sm, self.width, self.fp64_segments, self.native_match, self.ept)
 
 
 def cox_batch_workspace(num_arrays) -> int:
@@ -207,6 +212,16 @@ def cox_batch_prepare(num_arrays, h_lens, d_ws, ws_bytes, stream) -> int:
 def cox_batch_sum_hist(num_arrays, d_vals, d_keys, tune, d_ws, ws_bytes, d_sums, d_sums64, d_hists, stream) -> int:
     return lib().cox_batch_sum_hist(num_arrays, d_vals, d_keys, tune, d_ws, ws_bytes, d_sums, d_sums64, d_hists,
                                     stream)
+
+
+def cox_batch_percall_scratch(max_len) -> int:
+    return lib().cox_batch_percall_scratch(max_len)
+
+
+def cox_batch_percall(num_arrays, h_vals, h_keys, h_lens, d_sums, d_hists, d_scratch, scratch_bytes, events,
+                      stream) -> int:
+    return lib().cox_batch_percall(num_arrays, h_vals, h_keys, h_lens, d_sums, d_hists, d_scratch, scratch_bytes,
+                                   events, stream)
 
 
 def cox_batch_graph_create(num_arrays, d_vals, d_keys, tune, d_ws, ws_bytes, d_sums, d_sums64, d_hists, out) -> int:

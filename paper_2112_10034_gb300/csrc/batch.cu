@@ -17,6 +17,7 @@
 // A second small kernel folds each array's pairs in CTA order, in FP64 when
 // the array spans at least `fp64_segments` CTAs.  Every result depends only on
 // the data, E and G: never on timing or on the order CTAs run in.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -29,7 +30,7 @@ namespace cox {
 constexpr int kBatchBins = 256;
 constexpr int kBatchMaxCtas = 4096;
 constexpr size_t kBatchHeader = 256;
-constexpr cox_batch_tune kDefaultTune = {512, 2, 32, 8, 3};
+constexpr cox_batch_tune kDefaultTune = {512, 2, 32, 8, 3, 8};
 constexpr size_t kBatchSmemPerSm = 220 * 1024;  // dynamic shared memory the CTAs of one SM may take
 
 __host__ __device__ __forceinline__ int64_t cta_begin(int64_t i, int64_t E, int64_t G) {
@@ -98,7 +99,7 @@ __device__ __forceinline__ void fold(Pair& acc, float x) { acc = Comp::op(acc, C
 // One segment [s0, s1) of one array, all warps of the CTA.  Warp-uniform
 // loops: every lane of a warp runs every match_any step (invalid lanes take
 // part with valid = false).
-template <int W, int PEER, int S>
+template <int W, int PEER, int S, int H>
 __device__ void batch_segment(const float* __restrict__ v, const int32_t* __restrict__ k, int64_t s0, int64_t s1,
                               Pair& acc, uint32_t* my, uint32_t* tab, int& parity) {
   const int lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -130,14 +131,16 @@ __device__ void batch_segment(const float* __restrict__ v, const int32_t* __rest
     batch_hist_step<W, PEER, S>(key, ok, my, tab, parity);
   }
   // body: warp steps of 128 elements (one 128-bit load of values and of keys
-  // per lane), two steps in flight
+  // per lane), H steps in flight (4H elements per thread per round: the tuned
+  // "elements per thread"); a thread folds its elements in the same order for
+  // every H
   const int64_t stride = (int64_t)nw * 128;
-  for (int64_t q = vb + (int64_t)warp * 128; q < ve; q += 2 * stride) {
-    float x[8];
-    uint32_t key[8];
-    bool ok[8];
+  for (int64_t q = vb + (int64_t)warp * 128; q < ve; q += H * stride) {
+    float x[4 * H];
+    uint32_t key[4 * H];
+    bool ok[4 * H];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < H; ++h) {
       const int64_t e = q + h * stride + 4 * lane;
       if (e + 4 <= ve) {
         const float4 a = __ldcs(reinterpret_cast<const float4*>(v + e));
@@ -156,14 +159,14 @@ __device__ void batch_segment(const float* __restrict__ v, const int32_t* __rest
       }
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
+    for (int j = 0; j < 4 * H; ++j)
       if (ok[j]) fold(acc, x[j]);
-    batch_hist_quad<W, PEER, S>(key, ok, my, tab, parity);
-    batch_hist_quad<W, PEER, S>(key + 4, ok + 4, my, tab, parity);
+#pragma unroll
+    for (int h = 0; h < H; ++h) batch_hist_quad<W, PEER, S>(key + 4 * h, ok + 4 * h, my, tab, parity);
   }
 }
 
-template <int W, int PEER, int S>
+template <int W, int PEER, int S, int H>
 __global__ void __launch_bounds__(1024) k_batch_sum_hist(const float* const* __restrict__ vals,
                                                          const int32_t* const* __restrict__ keys,
                                                          const int64_t* __restrict__ off, int64_t A,
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(1024) k_batch_sum_hist(const float* const* __r
     const int64_t base = off[a];
     const int64_t end = min(hi, off[a + 1]);
     Pair acc = Comp::ident();
-    batch_segment<W, PEER, S>(vals[a], keys[a], pos - base, end - base, acc, my, tab, parity);
+    batch_segment<W, PEER, S, H>(vals[a], keys[a], pos - base, end - base, acc, my, tab, parity);
     const Pair s = block_reduce32<Comp>(acc, wpart);  // ends with __syncthreads
     if (threadIdx.x == 0) part[a + blockIdx.x] = make_float2(s.s, s.e);
     for (int b = threadIdx.x; b < kBatchBins; b += blockDim.x) {
@@ -247,7 +250,7 @@ __global__ void k_batch_combine(const int64_t* __restrict__ off, int64_t A, int 
 bool tune_ok(const cox_batch_tune& t) {
   return t.block_dim >= 64 && t.block_dim <= 1024 && t.block_dim % 32 == 0 && t.ctas_per_sm >= 1 &&
          t.ctas_per_sm <= 8 && valid_width(t.width) && t.fp64_segments >= 1 &&
-         (t.native_match >= 0 && t.native_match <= 3);
+         (t.native_match >= 0 && t.native_match <= 3) && (t.ept == 4 || t.ept == 8 || t.ept == 16);
 }
 
 struct BatchWs {
@@ -264,10 +267,10 @@ BatchWs batch_layout(void* ws, int64_t A) {
   return w;
 }
 
-template <int W, int PEER, int S>
-cox_status launch_batch(int G, int block_dim, size_t smem, cudaStream_t st, const float* const* d_vals,
-                        const int32_t* const* d_keys, const BatchWs& w, int64_t num_arrays, int32_t* d_hists) {
-  auto k = k_batch_sum_hist<W, PEER, S>;
+template <int W, int PEER, int S, int H>
+cox_status launch_batch1(int G, int block_dim, size_t smem, cudaStream_t st, const float* const* d_vals,
+                         const int32_t* const* d_keys, const BatchWs& w, int64_t num_arrays, int32_t* d_hists) {
+  auto k = k_batch_sum_hist<W, PEER, S, H>;
   static size_t attr[kMaxDevices];  // per device: the dynamic shared size this kernel may take so far
   size_t& a = attr[device_index()];
   if (smem > a) {  // (static shared memory counts against the 48 KB default too)
@@ -277,6 +280,15 @@ cox_status launch_batch(int G, int block_dim, size_t smem, cudaStream_t st, cons
   }
   k<<<G, block_dim, smem, st>>>(d_vals, d_keys, w.off, num_arrays, w.part, d_hists);
   return launch_status();
+}
+
+// Elements per thread per round (4 per 128-bit step in flight): 4, 8 or 16.
+template <int W, int PEER, int S>
+cox_status launch_batch(int ept, int G, int block_dim, size_t smem, cudaStream_t st, const float* const* d_vals,
+                        const int32_t* const* d_keys, const BatchWs& w, int64_t num_arrays, int32_t* d_hists) {
+  if (ept == 4) return launch_batch1<W, PEER, S, 1>(G, block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
+  if (ept == 16) return launch_batch1<W, PEER, S, 4>(G, block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
+  return launch_batch1<W, PEER, S, 2>(G, block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
 }
 
 }  // namespace cox
@@ -337,19 +349,59 @@ extern "C" cox_status cox_batch_sum_hist(int64_t num_arrays, const float* const*
   const cox_status s = with_width(t.width, [&](auto wc) {
     constexpr int W = decltype(wc)::value;
     if (peer == 3 && tables == 4)
-      return launch_batch<W, 3, 4>(G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
+      return launch_batch<W, 3, 4>(t.ept, G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
     if (peer == 3 && tables == 2)
-      return launch_batch<W, 3, 2>(G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
-    if (peer == 3) return launch_batch<W, 3, 1>(G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
-    if (peer == 1) return launch_batch<W, 1, 1>(G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
-    if (peer == 2) return launch_batch<W, 2, 1>(G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
-    return launch_batch<W, 0, 1>(G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
+      return launch_batch<W, 3, 2>(t.ept, G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
+    if (peer == 3) return launch_batch<W, 3, 1>(t.ept, G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
+    if (peer == 1) return launch_batch<W, 1, 1>(t.ept, G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
+    if (peer == 2) return launch_batch<W, 2, 1>(t.ept, G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
+    return launch_batch<W, 0, 1>(t.ept, G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
   });
   if (s != COX_OK) return s;
   const int cb = 256;
   k_batch_combine<<<(unsigned)((num_arrays + cb - 1) / cb), cb, 0, st>>>(w.off, num_arrays, G, w.part,
                                                                         t.fp64_segments, d_sums, d_sums64);
   return launch_status();
+}
+
+// ------------------------------------------------------- one launch per array
+// The baseline the batched launch is measured against: the same results from
+// one compensated grid-scope reduction and one match histogram per array,
+// launched back to back from this loop on one stream.
+extern "C" size_t cox_batch_percall_scratch(int64_t max_len) {
+  if (max_len < 1) return 0;
+  return (cox_tile_reduce_workspace(COX_SCOPE_GRID, max_len, 256) + 255) & ~(size_t)255;
+}
+
+extern "C" cox_status cox_batch_percall(int64_t num_arrays, const float* const* h_vals, const int32_t* const* h_keys,
+                                        const int64_t* h_lens, float* d_sums, int32_t* d_hists, void* d_scratch,
+                                        size_t scratch_bytes, void* const* events, void* stream) {
+  if (num_arrays < 1 || !h_vals || !h_keys || !h_lens || !d_sums || !d_hists || !d_scratch) return COX_EINVAL;
+  int64_t max_len = 1;
+  for (int64_t a = 0; a < num_arrays; ++a) {
+    if (h_lens[a] < 0) return COX_EINVAL;
+    max_len = std::max<int64_t>(max_len, h_lens[a]);
+  }
+  if (scratch_bytes < cox_batch_percall_scratch(max_len)) return COX_ENOMEM;
+  cudaStream_t st = as_stream(stream);
+  for (int64_t a = 0; a < num_arrays; ++a) {
+    cox_status s = COX_OK;
+    if (h_lens[a] == 0) {
+      if (cudaMemsetAsync(d_sums + a, 0, sizeof(float), st) != cudaSuccess ||
+          cudaMemsetAsync(d_hists + a * kBatchBins, 0, kBatchBins * sizeof(int32_t), st) != cudaSuccess)
+        return COX_ECUDA;
+    } else {
+      s = cox_tile_reduce(COX_SUM, COX_F32, 32, 256, COX_SCOPE_GRID, h_vals[a], d_sums + a, h_lens[a],
+                          COX_F_COMPENSATED, nullptr, d_scratch, scratch_bytes, stream);
+      if (s == COX_OK)
+        s = cox_match_histogram(COX_I32, 32, 256, h_keys[a], h_lens[a], kBatchBins, d_hists + a * kBatchBins,
+                                nullptr, 0u, stream);
+    }
+    if (s != COX_OK) return s;
+    if (events && events[a] && cudaEventRecord(static_cast<cudaEvent_t>(events[a]), st) != cudaSuccess)
+      return COX_ECUDA;
+  }
+  return COX_OK;
 }
 
 // ------------------------------------------------------------------ graphs
@@ -449,11 +501,13 @@ extern "C" cox_status cox_batch_autotune(int64_t num_arrays, const float* const*
   const int blocks[] = {256, 512, 1024};
   const int cpsm[] = {1, 2, 4};
   const int widths[] = {8, 32};
+  const int epts[] = {4, 8, 16};
   for (int b : blocks)
     for (int c : cpsm)
-      for (int wdt : widths) {
+      for (int wdt : widths)
+        for (int e : epts) {
         if (b * c > 2048) continue;  // more threads than an SM holds
-        const cox_batch_tune t = {b, c, wdt, kDefaultTune.fp64_segments, kDefaultTune.native_match};
+        const cox_batch_tune t = {b, c, wdt, kDefaultTune.fp64_segments, kDefaultTune.native_match, e};
         rc = cox_batch_sum_hist(num_arrays, d_vals, d_keys, &t, d_workspace, workspace_bytes, d_sums, nullptr,
                                 d_hists, stream);  // warm-up
         if (rc != COX_OK) goto done;
@@ -488,9 +542,9 @@ extern "C" cox_status cox_batch_autotune(int64_t num_arrays, const float* const*
       rc = COX_EINVAL;
       goto done;
     }
-    std::fprintf(f, "%s|batch_sum_hist|%d|%d|%d,%d,%d,%d,%d|%.4f\n", gpu_name().c_str(), log2_bucket(num_arrays),
+    std::fprintf(f, "%s|batch_sum_hist|%d|%d|%d,%d,%d,%d,%d,%d|%.4f\n", gpu_name().c_str(), log2_bucket(num_arrays),
                  log2_bucket(E), win.block_dim, win.ctas_per_sm, win.width, win.fp64_segments, win.native_match,
-                 best_t);
+                 win.ept, best_t);
     std::fclose(f);
   }
 done:
@@ -512,8 +566,8 @@ extern "C" cox_status cox_batch_tune_lookup(const char* cache_path, int64_t num_
   while (std::fgets(line, sizeof line, f)) {
     if (std::strncmp(line, want.c_str(), want.size()) != 0) continue;
     cox_batch_tune c{};
-    if (std::sscanf(line + want.size(), "%d,%d,%d,%d,%d", &c.block_dim, &c.ctas_per_sm, &c.width, &c.fp64_segments,
-                    &c.native_match) == 5 &&
+    if (std::sscanf(line + want.size(), "%d,%d,%d,%d,%d,%d", &c.block_dim, &c.ctas_per_sm, &c.width, &c.fp64_segments,
+                    &c.native_match, &c.ept) == 6 &&
         tune_ok(c)) {
       t = c;
       found = true;  // the last matching line wins

@@ -83,6 +83,10 @@ def test_every_tune_agrees_and_is_deterministic(cox, width, block, cpsm, native)
     first = check(b, off, hv, hk).copy()
     second = b.run()[0].cpu().numpy()
     np.testing.assert_array_equal(first.view(np.uint32), second.view(np.uint32))
+    # elements per thread only changes how many loads are in flight: the same bits
+    for ept in (4, 16):
+        e = cox.Batch(vals, keys, tune=(block, cpsm, width, 8, native, ept))
+        np.testing.assert_array_equal(check(e, off, hv, hk).view(np.uint32), first.view(np.uint32))
 
 
 def test_fp64_combine_for_every_array(cox):
@@ -137,6 +141,9 @@ def test_batch_argument_checks(cox):
     t = cox.cox_batch_tune(100, 2, 32, 8, 0)  # block not a multiple of 32
     assert cox.cox_batch_sum_hist(2, 16, 16, ctypes.addressof(t), ws.data_ptr(), 1 << 20, 16, None, 16,
                                   None) == cox.COX_EINVAL
+    t = cox.cox_batch_tune(256, 2, 32, 8, 0, 5)  # elements per thread not 4, 8 or 16
+    assert cox.cox_batch_sum_hist(2, 16, 16, ctypes.addressof(t), ws.data_ptr(), 1 << 20, 16, None, 16,
+                                  None) == cox.COX_EINVAL
 
 
 def test_batch_full_length_law_sample(cox):
@@ -146,3 +153,27 @@ def test_batch_full_length_law_sample(cox):
     vals, keys, off, hv, hk = make_arrays(lens, seed=inputs.BASE_SEED + 30, misalign=False)
     b = cox.Batch(vals, keys)
     check(b, off, hv, hk)
+
+
+def test_per_array_launches_match_the_oracle(cox):
+    """cox_batch_percall, the one-launch-per-array baseline, gives the same
+    histograms and sums within the tolerance (a different order of additions),
+    empty arrays included."""
+    import torch
+    lens = list(inputs.loguniform_lengths(60, 32, 1 << 16, seed=4)) + [0, 1, 5]
+    vals, keys, off, hv, hk = make_arrays(lens, seed=400)
+    A = len(lens)
+    h_vals = (ctypes.c_void_p * A)(*[v.data_ptr() for v in vals])
+    h_keys = (ctypes.c_void_p * A)(*[k.data_ptr() for k in keys])
+    h_lens = np.array(lens, dtype=np.int64)
+    sums = torch.full((A,), float("nan"), dtype=torch.float32, device="cuda")
+    hists = torch.full((A, 256), -1, dtype=torch.int32, device="cuda")
+    scr_b = cox.cox_batch_percall_scratch(int(max(lens)))
+    scr = torch.empty(scr_b, dtype=torch.uint8, device="cuda")
+    assert cox.cox_batch_percall(A, h_vals, h_keys, h_lens.ctypes.data, sums.data_ptr(), hists.data_ptr(),
+                                 scr.data_ptr(), scr_b, None, None) == cox.COX_OK
+    ref, ab, want = o.batch_ref(off, hv, hk)
+    np.testing.assert_array_equal(hists.cpu().numpy(), want)
+    assert o.rel_err(sums.cpu().numpy(), ref, ab).max() <= TOL
+    assert cox.cox_batch_percall(A, h_vals, h_keys, h_lens.ctypes.data, sums.data_ptr(), hists.data_ptr(),
+                                 scr.data_ptr(), 8, None, None) == cox.COX_ENOMEM
