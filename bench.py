@@ -774,7 +774,9 @@ def _err_stats(y, ref, ab):
 def oracle_precision(x_host, outs):
     """Part of the oracle leg (outside every timed region): the error of each
     of the 8 timed scans' outputs, as they stand after the last timed step,
-    against the oracle's FP64 tile prefix of the same 2^26 inputs."""
+    against the oracle's FP64 tile prefix of the same 2^26 inputs, and
+    whether they equal the oracle's fp32 emulation of the stated order bit
+    for bit (a check of this run's outputs)."""
     import oracle as o
     rows, refs = {}, {}
     for (w, comp), out in zip(VARIANTS, outs):
@@ -782,9 +784,15 @@ def oracle_precision(x_host, outs):
             _, ref, ab = o.scan_ref(o.SUM, o.F32, w, x_host)
             refs = {w: (ref, ab)}
         ref, ab = refs[w]
-        e = _err_stats(out.cpu().numpy(), ref, ab)
-        rows[f"W{w}_{'comp' if comp else 'plain'}"] = {k: float(f"{v:.3e}") for k, v in e.items()}
-        rows[f"W{w}_{'comp' if comp else 'plain'}"]["meets_1e-5"] = e["max"] <= 1e-5
+        y = out.cpu().numpy()
+        e = _err_stats(y, ref, ab)
+        row = {k: float(f"{v:.3e}") for k, v in e.items()}
+        row["meets_1e-5"] = e["max"] <= 1e-5
+        # the kernels follow the stated association order: the oracle's fp32
+        # emulation of that order must give the same bits at every output
+        row["bits_equal_oracle_emulation"] = bool(np.array_equal(
+            y.view(np.uint32), o.scan_emulate(o.SUM, o.F32, w, BLOCK, x_host, comp).view(np.uint32)))
+        rows[f"W{w}_{'comp' if comp else 'plain'}"] = row
     return {"reference": "oracle FP64 tile prefix (Neumaier) of the same 2^26 fp32 inputs",
             "metric": "max = max |y-r|/max(|r|, 2^-24 sum|x|) (the 1e-5 bar, gated for compensated); "
                       "pointwise over r != 0; normwise ||y-r||_2/||r||_2",

@@ -172,8 +172,10 @@ cox_status cox_tile_scan(cox_op op, cox_dtype dt, int width, int block_dim, cons
  *   zeroed by the call (cudaMemsetAsync).  Not shared across concurrent calls.
  * Integer results are exact.  GRID fp32 results take each tile's prefix in
  * the order its look-back found the predecessors' values, so their last bits
- * may differ from run to run (within the stated tolerance); BLOCK results are
- * reproducible.  Look-back waits are bounded as in cox_ballot_compact.
+ * may differ from run to run (within the stated tolerance); a compensated
+ * prefix passes between tiles with its error word rounded to 21 mantissa
+ * bits (about 2^-46 of the sum).  BLOCK results are reproducible.
+ * Look-back waits are bounded as in cox_ballot_compact.
  */
 cox_status cox_scan(cox_op op, cox_dtype dt, cox_scope scope, int block_dim, const void* d_in, void* d_out,
                     int64_t n, unsigned flags, int exclusive, void* d_workspace, size_t workspace_bytes,

@@ -299,83 +299,88 @@ __device__ unsigned look_back_sum2(uint64_t* desc, uint64_t* gdesc, uint64_t* ga
   return prefix;
 }
 
-// Two-level look-back for any scan value (pairs included).  Per tile: a
-// flag (1 aggregate, 2 inclusive prefix) and the two value slots of
-// look_back_op.  Per group of 32 tiles: an arrival counter, a flag and the
-// same two slots.  The tile whose arrival completes its group folds the
-// group's 32 aggregates (in tile order, so the group value does not depend
-// on arrival order) and publishes the group aggregate; the group's last
-// tile publishes its inclusive prefix as the group's.  The look-back reads
-// the tile's own group, then whole groups, 32 per window.  Called by a
-// whole warp; returns the exclusive prefix.
-struct GroupWs {
-  uint32_t* gflag;
-  uint32_t* gcnt;
-  uint64_t* gagg;
-  uint64_t* ginc;
-};
-
+// Look-back state and value in one 64-bit word, so a predecessor costs one
+// load: bits 62-63 the state (1 aggregate, 2 inclusive prefix), below them
+// the value -- a 32-bit value as is; a compensated pair as its sum word (bits
+// 0-31) and its error word rounded to 21 mantissa bits (bits 32-61).  The
+// rounding of an error word is at most 2^-22 of it, about 2^-46 of the sum:
+// far below the 1e-5 bar.  Tile aggregates also go, exact, to their own slot
+// for the group fold.
 template <class R>
-__device__ typename R::V look_back_op2(uint32_t* flags, uint64_t* agg, uint64_t* inc, GroupWs gw, int64_t tile,
-                                       int64_t ntiles, typename R::V total, uint32_t limit, unsigned* status,
-                                       bool& gave_up) {
+__device__ __forceinline__ uint64_t pk_word(uint64_t state, typename R::V v) {
+  if constexpr (R::kComp) {
+    const uint32_t eb = __float_as_uint(v.e);
+    // round to nearest on the 30-bit field; a carry into the exponent is the
+    // correct rounding up to the next binade
+    const uint64_t e30 = ((uint64_t)eb + 2u) >> 2;
+    return (state << 62) | ((e30 & 0x3FFFFFFFull) << 32) | (uint64_t)__float_as_uint(v.s);
+  } else {
+    return (state << 62) | (uint64_t)to_bits(v);
+  }
+}
+template <class R>
+__device__ __forceinline__ typename R::V pk_value(uint64_t w) {
+  using T = typename R::T;
+  if constexpr (R::kComp) return Pair{__uint_as_float((uint32_t)w), __uint_as_float((uint32_t)((w >> 32) << 2))};
+  else return from_bits<T>((uint32_t)w);
+}
+
+// Two-level look-back over packed words (any value except 32-bit sums, which
+// take look_back_sum2).  word[t]: the tile's state|value; agg[t]: its exact
+// aggregate; per group of 32 tiles gword[g] (state|value, only growing:
+// atomicMax, and a prefix word is above any aggregate word) and an arrival
+// counter gcnt[g].  The tile whose arrival completes its group folds the
+// group's 32 aggregates in tile order and publishes the group aggregate; the
+// group's last tile publishes its inclusive prefix as the group's.  Called by
+// a whole warp; returns the exclusive prefix.
+template <class R>
+__device__ typename R::V look_back_pk(uint64_t* word, uint64_t* agg, uint64_t* gword, uint32_t* gcnt, int64_t tile,
+                                      int64_t ntiles, typename R::V total, uint32_t limit, unsigned* status,
+                                      bool& gave_up) {
   using V = typename R::V;
   const int lane = lane_id();
   gave_up = false;
   const int64_t g = tile >> 5;
   const int pos = (int)(tile & 31);
   const int64_t g0 = g << 5;
-  // ---- publish the aggregate; the group's completing tile publishes the group's
-  if (lane == 0) {
-    if (tile == 0) {
-      st_relaxed_u64(inc, pack<R>(total));
-      st_relaxed_u64(agg, pack<R>(total));
-      st_release_u32(flags, 2u);
-    } else {
-      st_relaxed_u64(agg + tile, pack<R>(total));
-      st_release_u32(flags + tile, 1u);
-    }
-  }
   int last = 0;
   if (lane == 0) {
+    st_relaxed_u64(agg + tile, pack<R>(total));
+    st_relaxed_u64(word + tile, pk_word<R>(tile == 0 ? 2u : 1u, total));
     __threadfence();
     const int64_t gsize = min((int64_t)32, ntiles - g0);
-    last = (int64_t)atomicAdd(gw.gcnt + g, 1u) + 1 == gsize;
+    last = (int64_t)atomicAdd(gcnt + g, 1u) + 1 == gsize;
     if (last) __threadfence();
   }
   if (__shfl_sync(kFull, last, 0)) {
     const int64_t gsize = min((int64_t)32, ntiles - g0);
     V v = lane < gsize ? unpack<R>(ld_relaxed_u64(agg + g0 + lane)) : R::ident();
     v = warp_fold<R>(v);
-    if (lane == 0) {
-      st_relaxed_u64(gw.gagg + g, pack<R>(v));
-      __threadfence();
-      atomicCAS(gw.gflag + g, 0u, 1u);  // a published inclusive prefix (2) stays
-    }
+    if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(gword + g), pk_word<R>(1u, v));
   }
   V prefix = R::ident();
   uint32_t polls = 0;
   bool timed_out = false;
   bool done = tile == 0;
   if (!done && pos > 0) {  // own group: lane l holds position l < pos
-    uint32_t f = lane < pos ? ld_acquire_u32(flags + g0 + lane) : 1u;
+    uint64_t w = lane < pos ? ld_relaxed_u64(word + g0 + lane) : (1ull << 62);
     unsigned pm;
     int fl;
     for (;;) {
-      pm = __ballot_sync(kFull, lane < pos && f == 2u);
+      pm = __ballot_sync(kFull, lane < pos && (w >> 62) == 2u);
       fl = pm ? 31 - __clz(pm) : -1;
-      const bool missing = lane < pos && lane > fl && f == 0u;
+      const bool missing = lane < pos && lane > fl && (w >> 62) == 0u;
       if (!__any_sync(kFull, missing)) break;
       if (++polls > limit) {
         timed_out = true;
         break;
       }
       if (polls > 64) __nanosleep(64);
-      if (missing) f = ld_acquire_u32(flags + g0 + lane);
+      if (missing) w = ld_relaxed_u64(word + g0 + lane);
     }
     if (!__any_sync(kFull, timed_out)) {
       V part = R::ident();
-      if (lane < pos && lane >= fl) part = unpack<R>(ld_relaxed_u64((lane == fl ? inc : agg) + g0 + lane));
+      if (lane < pos && lane >= fl) part = pk_value<R>(w);
       prefix = warp_fold<R>(part);
       done = fl >= 0;
     }
@@ -384,24 +389,24 @@ __device__ typename R::V look_back_op2(uint32_t* flags, uint64_t* agg, uint64_t*
     V gsum = R::ident();
     for (int64_t gw0 = g - 1;; gw0 -= 32) {
       const int64_t gi = gw0 - lane;
-      uint32_t f = gi >= 0 ? ld_acquire_u32(gw.gflag + gi) : 2u;  // before group 0: the identity
+      uint64_t w = gi >= 0 ? ld_relaxed_u64(gword + gi) : (2ull << 62) | pk_word<R>(0u, R::ident());
       unsigned pm;
       for (;;) {
-        pm = __ballot_sync(kFull, f == 2u);
+        pm = __ballot_sync(kFull, (w >> 62) == 2u);
         const int fl = pm ? __ffs(pm) - 1 : 32;
-        const bool missing = lane <= fl && f == 0u;
+        const bool missing = lane <= fl && (w >> 62) == 0u;
         if (!__any_sync(kFull, missing)) break;
         if (++polls > limit) {
           timed_out = true;
           break;
         }
         if (polls > 64) __nanosleep(64);
-        if (missing && gi >= 0) f = ld_acquire_u32(gw.gflag + gi);
+        if (missing && gi >= 0) w = ld_relaxed_u64(gword + gi);
       }
       if (__any_sync(kFull, timed_out)) break;
       const int fl = pm ? __ffs(pm) - 1 : 32;
       V part = R::ident();
-      if (lane <= fl && gi >= 0) part = unpack<R>(ld_relaxed_u64((f == 2u ? gw.ginc : gw.gagg) + gi));
+      if (lane <= fl && gi >= 0) part = pk_value<R>(w);
       gsum = R::op(warp_fold<R>(part), gsum);  // older windows on the left
       if (pm) break;
     }
@@ -411,27 +416,15 @@ __device__ typename R::V look_back_op2(uint32_t* flags, uint64_t* agg, uint64_t*
     gave_up = true;
     if (lane == 0) {
       atomicOr(status, (unsigned)kDevTimeout);
-      st_relaxed_u64(inc + tile, pack<R>(total));  // release successors
-      st_release_u32(flags + tile, 2u);
-      if (pos == 31) {
-        st_relaxed_u64(gw.ginc + g, pack<R>(total));
-        __threadfence();
-        atomicMax(gw.gflag + g, 2u);
-      }
+      st_relaxed_u64(word + tile, pk_word<R>(2u, total));  // release successors
+      if (pos == 31) atomicMax(reinterpret_cast<unsigned long long*>(gword + g), pk_word<R>(2u, total));
     }
     return R::ident();
   }
   if (lane == 0) {
     const V incl = R::op(prefix, total);
-    if (tile != 0) {
-      st_relaxed_u64(inc + tile, pack<R>(incl));
-      st_release_u32(flags + tile, 2u);
-    }
-    if (pos == 31) {
-      st_relaxed_u64(gw.ginc + g, pack<R>(incl));
-      __threadfence();
-      atomicMax(gw.gflag + g, 2u);
-    }
+    if (tile != 0) st_relaxed_u64(word + tile, pk_word<R>(2u, incl));
+    if (pos == 31) atomicMax(reinterpret_cast<unsigned long long*>(gword + g), pk_word<R>(2u, incl));
   }
   return prefix;
 }
@@ -622,20 +615,20 @@ __global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ 
         atomicOr(status, (unsigned)kDevTimeout);
         mbar_wait_bounded(&s_bar, 0u, limit);
         if constexpr (!std::is_same<R, Plain<AddU>>::value) {
-          st_relaxed_u64(inc + tile, pack<R>(R::ident()));
+          // a zero prefix for successors; the group level counts this tile's
+          // arrival and, if it completes the group, publishes some aggregate
+          // (the device status already says the results are not to be used)
+          const int64_t ngroups = (ntiles + 31) / 32, g = tile >> 5;
+          const int64_t gsize = min((int64_t)32, ntiles - (g << 5));
+          uint64_t* gword = inc + ntiles;
+          uint32_t* gcnt = reinterpret_cast<uint32_t*>(gword + ngroups);
           st_relaxed_u64(agg + tile, pack<R>(R::ident()));
-          st_release_u32(flags + tile, 2u);
-          // group level: count this tile's arrival; the group slots then hold a partial fold, and the
-          // device status already says the results are not to be used
-          const int64_t ngroups = (ntiles + 31) / 32;
-          uint64_t* ginc = inc + ntiles;
-          uint32_t* gflag = reinterpret_cast<uint32_t*>(ginc + 2 * ngroups);
-          atomicAdd(gflag + ngroups + (tile >> 5), 1u);
-          if ((tile & 31) == 31) {
-            st_relaxed_u64(ginc + (tile >> 5), pack<R>(R::ident()));
-            __threadfence();
-            atomicMax(gflag + (tile >> 5), 2u);
-          }
+          st_relaxed_u64(inc + tile, pk_word<R>(2u, R::ident()));
+          __threadfence();
+          if ((int64_t)atomicAdd(gcnt + g, 1u) + 1 == gsize)
+            atomicMax(reinterpret_cast<unsigned long long*>(gword + g), pk_word<R>(1u, R::ident()));
+          if ((tile & 31) == 31)
+            atomicMax(reinterpret_cast<unsigned long long*>(gword + g), pk_word<R>(2u, R::ident()));
         } else {
           st_relaxed_u64(agg + tile, (2ull << 32) | to_bits(R::ident()));
           if constexpr (std::is_same<R, Plain<AddU>>::value) {  // keep the group level consistent
@@ -717,13 +710,11 @@ __global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ 
       // group descriptors and accumulators after the tile slots
       prefix = look_back_sum2(agg, inc + ntiles, inc + ntiles + ngroups, tile, ntiles, total, limit, status, gave_up);
     } else {
-      // group slots after the tile slots: ginc, gagg (64-bit), then gflag, gcnt (32-bit)
-      GroupWs gw;
-      gw.ginc = inc + ntiles;
-      gw.gagg = gw.ginc + ngroups;
-      gw.gflag = reinterpret_cast<uint32_t*>(gw.gagg + ngroups);
-      gw.gcnt = gw.gflag + ngroups;
-      prefix = look_back_op2<R>(flags, agg, inc, gw, tile, ntiles, total, limit, status, gave_up);
+      // packed tile words in `inc`, exact aggregates in `agg`; after the tile
+      // slots the group words (64-bit), then the group arrival counters
+      uint64_t* gword = inc + ntiles;
+      uint32_t* gcnt = reinterpret_cast<uint32_t*>(gword + ngroups);
+      prefix = look_back_pk<R>(inc, agg, gword, gcnt, tile, ntiles, total, limit, status, gave_up);
     }
     if (lane == 0) {
 #pragma unroll
