@@ -405,7 +405,9 @@ typedef struct {
                         per-warp table in shared memory (lanes OR their bit into their key's
                         word in their tile's copy of the table; the lane that found the word
                         empty takes the mask and clears it), or from the ballots of 0 where
-                        that table (2 x 32 / width x 1 KB per warp) does not fit an SM */
+                        that table (2 x 32 / width x 1 KB per warp) does not fit an SM;
+                        4 the same as 3 with the width-32 masks split over two words by lane
+                        half (fewer lanes on a hot key's word) and one set of tables */
   int ept;           /* elements per thread per round: 4, 8 or 16 (128-bit loads in flight per
                         thread: ept / 4); the fold order, and so every result, is the same for all */
 } cox_batch_tune;
@@ -472,8 +474,8 @@ void cox_graph_destroy(cox_graph* g);
 
 /*
  * cox_batch_autotune -- times every candidate tune (block_dim 256/512/1024 x
- * ctas_per_sm 1/2/4 x width 8/32 x elements per thread 4/8/16; fp64_segments
- * 8 and the table-built peer masks, native_match 3, in every candidate) on
+ * ctas_per_sm 1/2/4 x width 8/32 x elements per thread 4/8/16 x table-built
+ * peer masks 3/4; fp64_segments 8 in every candidate) on
  * this batch (prepared in d_workspace) with CUDA events, `reps` timed runs
  * each, and returns the fastest in *best (and its mean milliseconds in
  * *best_ms if non-NULL).  If cache_path is not NULL the winner is appended to

@@ -57,10 +57,10 @@ __device__ __forceinline__ void batch_hist_step(uint32_t key, bool valid, uint32
   const bool in = valid && key < (uint32_t)kBatchBins;
   if constexpr (PEER == 2) {
     if (in) atomicAdd(my + key, 1u);
-  } else if constexpr (PEER == 3) {
+  } else if constexpr (PEER == 3 || PEER == 4) {
     const uint32_t k1[1] = {key};
     const bool in1[1] = {in};
-    hist_peer_table<W, 1, 1, false, S>(k1, in1, kBatchBins, my, tab, parity);  // the first table of a set
+    hist_peer_table<W, 1, 1, PEER == 4, S>(k1, in1, kBatchBins, my, tab, parity);  // the first table (of a set)
   } else {
     const unsigned tmask = W == 32 ? kFull : (((1u << W) - 1u) << (lane & ~(W - 1)));
     const unsigned lt = lanemask_lt();
@@ -79,7 +79,7 @@ __device__ __forceinline__ void batch_hist_step(uint32_t key, bool valid, uint32
 template <int W, int PEER, int S>
 __device__ __forceinline__ void batch_hist_quad(const uint32_t* key, const bool* ok, uint32_t* my, uint32_t* tab,
                                                 int& parity) {
-  if constexpr (PEER == 3) {
+  if constexpr (PEER == 3 || PEER == 4) {
     uint32_t k4[4];
     bool in4[4];
 #pragma unroll
@@ -87,7 +87,7 @@ __device__ __forceinline__ void batch_hist_quad(const uint32_t* key, const bool*
       k4[j] = key[j];
       in4[j] = ok[j] && key[j] < (uint32_t)kBatchBins;
     }
-    hist_peer_table<W, S, 4, false>(k4, in4, kBatchBins, my, tab, parity);
+    hist_peer_table<W, S, 4, PEER == 4>(k4, in4, kBatchBins, my, tab, parity);
   } else {
 #pragma unroll
     for (int j = 0; j < 4; ++j) batch_hist_step<W, PEER, S>(key[j], ok[j], my, tab, parity);
@@ -174,7 +174,9 @@ __global__ void __launch_bounds__(1024) k_batch_sum_hist(const float* const* __r
   extern __shared__ __align__(16) uint32_t sh[];  // (blockDim / 32) x 256 per-warp bins, then the peer tables
   __shared__ Pair wpart[32];
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
-  const int ntab = PEER == 3 ? 2 * S * (int)hist_table_words(W, kBatchBins, false) : 0;  // peer tables per warp
+  const int ntab = PEER == 3   ? 2 * S * (int)hist_table_words(W, kBatchBins, false)  // two sets of S
+                   : PEER == 4 ? S * (int)hist_table_words(W, kBatchBins, true)        // S split tables
+                               : 0;  // peer tables per warp
   for (int i = threadIdx.x; i < nw * (kBatchBins + ntab); i += blockDim.x) sh[i] = 0u;
   __syncthreads();
   uint32_t* tab = sh + nw * kBatchBins + warp * ntab;
@@ -250,7 +252,7 @@ __global__ void k_batch_combine(const int64_t* __restrict__ off, int64_t A, int 
 bool tune_ok(const cox_batch_tune& t) {
   return t.block_dim >= 64 && t.block_dim <= 1024 && t.block_dim % 32 == 0 && t.ctas_per_sm >= 1 &&
          t.ctas_per_sm <= 8 && valid_width(t.width) && t.fp64_segments >= 1 &&
-         (t.native_match >= 0 && t.native_match <= 3) && (t.ept == 4 || t.ept == 8 || t.ept == 16);
+         (t.native_match >= 0 && t.native_match <= 4) && (t.ept == 4 || t.ept == 8 || t.ept == 16);
 }
 
 struct BatchWs {
@@ -337,14 +339,19 @@ extern "C" cox_status cox_batch_sum_hist(int64_t num_arrays, const float* const*
   // hist_table_words words per warp): four per set where that leaves room for
   // ctas_per_sm CTAs on an SM, else two, else one
   const size_t bins_bytes = (size_t)(t.block_dim / 32) * kBatchBins * sizeof(uint32_t);
-  const size_t tab_bytes =  // one table of each of the two sets
-      (size_t)(t.block_dim / 32) * 2 * hist_table_words(t.width, kBatchBins, false) * sizeof(uint32_t);
+  const size_t tab_bytes =  // per table round: one table of each of the two sets, or one split table
+      (size_t)(t.block_dim / 32) *
+      (t.native_match == 4 ? hist_table_words(t.width, kBatchBins, true)
+                           : 2 * hist_table_words(t.width, kBatchBins, false)) *
+      sizeof(uint32_t);
   // (tables that do not fit one SM at all: the same masks from ballots)
-  const int peer = t.native_match == 3 && bins_bytes + tab_bytes > kBatchSmemPerSm ? 0 : t.native_match;
+  const bool table = t.native_match == 3 || t.native_match == 4;
+  const int peer = table && bins_bytes + tab_bytes > kBatchSmemPerSm ? 0 : t.native_match;
   int tables = 0;
-  if (peer == 3)
+  if (peer == 3 || peer == 4)
     for (tables = 4; tables > 1 && (bins_bytes + tables * tab_bytes) * (size_t)t.ctas_per_sm > kBatchSmemPerSm;)
       tables >>= 1;
+  if (peer == 4 && tables > 2) tables = 2;  // (split tables: one or two per round)
   const size_t smem = bins_bytes + (size_t)tables * tab_bytes;
   const cox_status s = with_width(t.width, [&](auto wc) {
     constexpr int W = decltype(wc)::value;
@@ -353,6 +360,9 @@ extern "C" cox_status cox_batch_sum_hist(int64_t num_arrays, const float* const*
     if (peer == 3 && tables == 2)
       return launch_batch<W, 3, 2>(t.ept, G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
     if (peer == 3) return launch_batch<W, 3, 1>(t.ept, G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
+    if (peer == 4 && tables >= 2)
+      return launch_batch<W, 4, 2>(t.ept, G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
+    if (peer == 4) return launch_batch<W, 4, 1>(t.ept, G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
     if (peer == 1) return launch_batch<W, 1, 1>(t.ept, G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
     if (peer == 2) return launch_batch<W, 2, 1>(t.ept, G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
     return launch_batch<W, 0, 1>(t.ept, G, t.block_dim, smem, st, d_vals, d_keys, w, num_arrays, d_hists);
@@ -502,12 +512,14 @@ extern "C" cox_status cox_batch_autotune(int64_t num_arrays, const float* const*
   const int cpsm[] = {1, 2, 4};
   const int widths[] = {8, 32};
   const int epts[] = {4, 8, 16};
+  const int peers[] = {3, 4};
   for (int b : blocks)
     for (int c : cpsm)
       for (int wdt : widths)
-        for (int e : epts) {
+        for (int e : epts)
+          for (int pm : peers) {
         if (b * c > 2048) continue;  // more threads than an SM holds
-        const cox_batch_tune t = {b, c, wdt, kDefaultTune.fp64_segments, kDefaultTune.native_match, e};
+        const cox_batch_tune t = {b, c, wdt, kDefaultTune.fp64_segments, pm, e};
         rc = cox_batch_sum_hist(num_arrays, d_vals, d_keys, &t, d_workspace, workspace_bytes, d_sums, nullptr,
                                 d_hists, stream);  // warm-up
         if (rc != COX_OK) goto done;

@@ -73,7 +73,7 @@ def test_batch_matches_the_oracle(cox):
     check(b, off, hv, hk)
 
 
-@pytest.mark.parametrize("native", [0, 1, 2, 3])
+@pytest.mark.parametrize("native", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("width", [2, 8, 32])
 @pytest.mark.parametrize("block,cpsm", [(64, 1), (256, 2), (512, 4), (1024, 1), (128, 8)])
 def test_every_tune_agrees_and_is_deterministic(cox, width, block, cpsm, native):
