@@ -280,13 +280,22 @@ cox_status cox_vote_stats(cox_dtype dt, int width, const void* d_pred, int64_t n
  * 2^32).  d_out: batch*height*width uint32.  d_workspace:
  * cox_integral_image_workspace() bytes (per image row a word per 32-pixel
  * strip; per image, band of 64 rows and column a word; per image, band and
- * 128 columns a word), 16-byte aligned.  Rows are cut into bands of 64 and
- * strips; per (image, band, strip) one warp first sums its block (row
- * totals, column prefixes, block total), then one warp walks the band's
- * rows from the integral above it (row scan plus the row's prefix left of
- * the strip, running column sums).  16-byte aligned input and output whose
- * rows are whole 16-byte units read the pixels twice; other layouts take a
- * three-pass form that reads them three times.
+ * 128 columns a word), 16-byte aligned; its contents need no preparation
+ * and are scratch after the call.
+ * Three forms, chosen on the host from the layout and size:
+ *  - strip walk (16-byte aligned input and output, rows of whole 16-byte
+ *    units, at least 4 x SMs strips of 128 columns in all and at most 64 per
+ *    row): one cooperative launch, every pixel read once.  Three warps per
+ *    (image, strip) walk the strip top to bottom through a TMA ring; the
+ *    integral just left of the strip comes from the left strips' per-row
+ *    totals, published as tagged words (the call zeroes them first with a
+ *    cudaMemsetAsync on `stream`).  A wait for a neighbour's words or a ring
+ *    stage that runs out records COX_ETIMEOUT for cox_device_status() and
+ *    leaves the output incomplete.  COX_ECUDA if the launch is refused.
+ *  - band form (same layout, fewer strips): rows cut into bands of 64; per
+ *    (image, band, strip) one warp sums its block, then one warp walks the
+ *    band's rows from the integral above it; pixels read twice.
+ *  - three-pass form (any other layout): pixels read three times.
  */
 cox_status cox_integral_image(cox_dtype in_dt, int64_t batch, int64_t height, int64_t width, const void* d_in,
                               uint32_t* d_out, void* d_workspace, size_t workspace_bytes, void* stream);

@@ -61,7 +61,10 @@ def test_vote_stats_fp32_zeros_and_bad_args(cox):
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 7, 5), (3, 33, 31), (2, 64, 64), (4, 100, 1000),
                                    (2, 1080, 1920), (1, 17, 4097), (3, 130, 1040), (1, 700, 2048),
-                                   (2, 65, 16), (2, 3, 132), (1, 64, 528), (5, 129, 4)])
+                                   (2, 65, 16), (2, 3, 132), (1, 64, 528), (5, 129, 4),
+                                   # enough 128-column strips for the strip walk: ragged strips and
+                                   # stages, several units per warp, more than 32 strips per row
+                                   (64, 70, 1920), (640, 37, 272), (40, 100, 3840), (40, 20, 4224)])
 @pytest.mark.parametrize("dt", ["u8", "u32"])
 def test_integral_image(cox, shape, dt):
     import torch
@@ -101,3 +104,22 @@ def test_integral_image_misaligned(cox, dt, in_off, out_off):
     np.testing.assert_array_equal(got[out_off:out_off + b * h * w].view(np.uint32).reshape(b, h, w),
                                   o.integral_image(img))
     assert (got[:out_off] == 0x7FBADBAD).all() and (got[out_off + b * h * w:] == 0x7FBADBAD).all()
+
+
+@pytest.mark.parametrize("dt", ["u8", "u32"])
+def test_integral_image_strip_walk_reuses_its_workspace(cox, dt):
+    """Two calls in a row on one workspace (the strip counters restart at 0
+    each call), the second on other pixels."""
+    import torch
+    b, h, w = 96, 45, 1040
+    code = cox.COX_U8 if dt == "u8" else cox.COX_U32
+    wsb = cox.cox_integral_image_workspace(b, h, w)
+    ws = torch.full((wsb,), 0xFF, dtype=torch.uint8, device="cuda")
+    for seed in (5, 6):
+        bits = inputs.bits_u32(b * h * w, seed=seed)
+        img = (bits & 0xFF).astype(np.uint8).reshape(b, h, w) if dt == "u8" else bits.reshape(b, h, w)
+        d_in = dev(img.view(np.uint8).ravel() if dt == "u8" else img.view(np.int32).ravel())
+        out = torch.empty(b * h * w, dtype=torch.int32, device="cuda")
+        assert cox.cox_integral_image(code, b, h, w, d_in.data_ptr(), out.data_ptr(), ws.data_ptr(), wsb, None) == 0
+        np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32).reshape(b, h, w), o.integral_image(img))
+    assert cox.cox_device_status(None) == cox.COX_OK
