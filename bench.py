@@ -846,7 +846,8 @@ def run_profile(args):
     elements); `gridscan` a 2^26 int32 grid-scope scan (`gridscan_comp`: fp32
     compensated); `reduce` a 2^26 fp32
     compensated tile reduce (W 32) then block reduce (B 256); `intimage` the
-    integral images of 64 8-bit 1080x1920 frames (two kernels); `filter` the
+    integral images of 64 8-bit 1080x1920 frames (a memset of the strip
+    totals, then the strip walk), `intimage32` the same with 32-bit pixels; `filter` the
     aggregated filter of 2^26 keys at density 0.5; `coalesced` the group
     size then the group shuffle over 2^26 half-active elements."""
     import torch
@@ -904,15 +905,16 @@ def run_profile(args):
                                     sh))
             chk(cox.cox_tile_reduce(0, 2, 32, 256, 1, x.data_ptr(), y.data_ptr(), N_ELEMS, 1, None, None, 0, sh))
         launches = reps * 2
-    elif args.profile == "intimage":
+    elif args.profile in ("intimage", "intimage32"):
         B, H, W = 64, 1080, 1920
-        img = torch.randint(0, 256, (B * H * W // 4,), device=dev, dtype=torch.int32)
+        code, words = (3, B * H * W // 4) if args.profile == "intimage" else (1, B * H * W)
+        img = torch.randint(0, 256, (words,), device=dev, dtype=torch.int32)
         ii = torch.empty(B * H * W, dtype=torch.int32, device=dev)
         wsb = cox.cox_integral_image_workspace(B, H, W)
         ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
         for _ in range(reps):
-            chk(cox.cox_integral_image(3, B, H, W, img.data_ptr(), ii.data_ptr(), ws.data_ptr(), wsb, sh))
-        launches = reps * 2
+            chk(cox.cox_integral_image(code, B, H, W, img.data_ptr(), ii.data_ptr(), ws.data_ptr(), wsb, sh))
+        launches = reps
     elif args.profile == "filter":
         k = torch.from_numpy(inputs.uniform_u31(N_ELEMS, inputs.BASE_SEED + 2)).to(dev)
         out = torch.empty(N_ELEMS, dtype=torch.int32, device=dev)
@@ -958,7 +960,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile", choices=["scan", "compact", "hist", "batch", "gridscan", "gridscan_comp", "reduce",
-                                          "intimage", "filter", "coalesced"],
+                                          "intimage", "intimage32", "filter", "coalesced"],
                     default=None,
                     help="small single-op case for ncu captures")
     args = ap.parse_args()
