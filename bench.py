@@ -44,7 +44,7 @@ WORKLOAD = ("tile inclusive scan (shfl_up, cg tiles) of 2^26 fp32 N(0,1) at widt
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture, valid
 # only while the kernel sources hash to `src_sha` (else reported as null).
-NCU_TRAFFIC = {"src_sha": "10c58d937cda7873",
+NCU_TRAFFIC = {"src_sha": "dc84082847ff3dcc",
                "bytes_per_launch": {
                                     "k_tile_scan_rows<Plain<AddF>, 16>": 268503296 + 216764416,
                                     "k_tile_scan_rows<Comp, 16>": 268482816 + 216979456,

@@ -649,10 +649,6 @@ __device__ __forceinline__ void scan_row_regs(typename R::V (&v)[32]) {
 }
 
 // ------------------------------------------------------------ host helpers
-// Tensor map of a 32-bit array viewed as `rows` rows of 32 elements (128 B),
-// boxes of 32 x `box_rows`, 128-byte swizzle: in shared memory the 16-byte
-// unit j of row r sits at unit j ^ (r & 7) of the row (conflict-free
-// per-lane row reads).  `base` must be 16-byte aligned; 1 <= rows < 2^31.
 // The driver's tensor-map encoder (looked up once; null if unavailable).
 inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
@@ -667,6 +663,10 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return encode;
 }
 
+// Tensor map of a 32-bit array viewed as `rows` rows of 32 elements (128 B),
+// boxes of 32 x `box_rows`, 128-byte swizzle: in shared memory the 16-byte
+// unit j of row r sits at unit j ^ (r & 7) of the row (conflict-free
+// per-lane row reads).  `base` must be 16-byte aligned; 1 <= rows < 2^31.
 inline bool encode_rows32_map(CUtensorMap* map, const void* base, int64_t rows, int box_rows) {
   const auto encode = tensor_map_encoder();
   if (!encode) return false;
