@@ -158,8 +158,9 @@ cox_status cox_tile_scan(cox_op op, cox_dtype dt, int width, int block_dim, cons
  * The step after the tile scan: the SDK's shfl_scan_test scans each block
  * with warp shuffle scans and a scan of the warp totals, and uniform_add adds
  * each block's prefix (Table 1).  BLOCK scope does the first part on blocks
- * of block_dim elements; GRID scope chains tiles of 16384 elements (8192 for
- * compensated sums) with the decoupled look-back of cox_ballot_compact: in a
+ * of block_dim elements; GRID scope chains tiles (16-byte aligned arrays:
+ * 8192 elements by TMA, 16384 for compensated sums; other layouts: 16384,
+ * 8192 compensated) with the decoupled look-back of cox_ballot_compact: in a
  * tile every warp scans its rows of 32 elements by shfl_up, carries row
  * totals across its rows, the warp totals are scanned, the tile publishes
  * its aggregate, looks back for its prefix and adds it.

@@ -5,9 +5,11 @@
 // shared memory, warp 0 scans them, and every element takes its warp's
 // prefix (the uniform_add step).
 //
-// GRID scope chains tiles with a decoupled look-back.  A CTA takes a tile
-// (16384 elements; 8192 for compensated sums, whose pairs need twice the
-// shared memory) from an atomic ticket, receives it by one TMA bulk copy,
+// GRID scope chains tiles with a decoupled look-back.  16-byte aligned
+// arrays take the row-tile kernel (k_scan_grid_rows, below); in any other
+// layout a CTA takes a tile (16384 elements; 8192 for compensated sums,
+// whose pairs need twice the shared memory) from an atomic ticket, receives
+// it by one TMA bulk copy,
 // and every warp scans its rows of 32 elements with shfl_up, carrying row
 // totals across its rows (eight rows at a time for instruction-level
 // parallelism).  Lane 0 of warp 0 scans the eight warp totals, the tile
@@ -429,6 +431,15 @@ __device__ typename R::V look_back_pk(uint64_t* word, uint64_t* agg, uint64_t* g
   return prefix;
 }
 
+// Rows per lane of the row-tile grid scan (tiles of RPL x 8192 elements):
+// one for 32-bit values (33 KB tiles, six CTAs per SM), two for compensated
+// pairs (their registers allow four CTAs per SM, and the larger tile halves
+// the look-backs).
+template <class R>
+__host__ __device__ constexpr int grid_rows_rpl() {
+  return R::kComp ? 2 : 1;
+}
+
 template <class R>
 __host__ __device__ constexpr int grid_scan_tile() {
   return R::kComp ? 8192 : 16384;
@@ -558,10 +569,11 @@ __global__ void __launch_bounds__(256) k_scan_grid(const uint32_t* __restrict__ 
   }
 }
 
-// GRID scope over aligned arrays of at least one full row: tiles of 512 rows
-// of 32 elements (16384) arrive by two 2D TMA boxes with 128-byte swizzle;
-// lane t of warp w owns rows 64w + t and 64w + 32 + t of the tile.  Pass A
-// folds each row (its total), shuffle scans over the warp's 64 rows and a
+// GRID scope over aligned arrays of at least one full row: tiles of RPL x 256
+// rows of 32 elements (grid_rows_rpl) arrive by RPL 2D TMA boxes with
+// 128-byte swizzle; lane t of warp w owns rows 32 (RPL w + j) + t, j < RPL,
+// of the tile.  Pass A folds each row (its total), shuffle scans over the
+// warp's rows and a
 // scan of the 8 warp totals give every row's exclusive prefix, the tile
 // looks back for its own prefix (32-bit values: packed state|value
 // descriptors in `agg`), and pass B re-reads the row, carrying
@@ -569,10 +581,9 @@ __global__ void __launch_bounds__(256) k_scan_grid(const uint32_t* __restrict__ 
 // Sums are folded left to right within a row, so fp32 results differ from
 // the shuffle form in their last bits (tolerance-checked).  The partial last
 // row (n % 32 elements) is read and written by its lane from global memory.
-constexpr int kGridRowsTile = 512;  // rows per tile: two TMA boxes of 256 rows
-constexpr int kGridBoxRows = 256;
+constexpr int kGridBoxRows = 256;  // rows per TMA box; a tile is RPL boxes (RPL rows per lane)
 
-template <class R>
+template <class R, int RPL>
 __global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ CUtensorMap tin,
                                                         const __grid_constant__ CUtensorMap tout,
                                                         const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
@@ -598,15 +609,19 @@ __global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ 
   __syncthreads();
   const int64_t tile = s_tile;
   if (tile >= ntiles) return;
-  const int64_t r0 = tile * kGridRowsTile;
-  const int nbox = r0 >= rows ? 0 : (r0 + kGridBoxRows >= rows ? 1 : 2);  // boxes holding full rows
+  constexpr int kTileRows = RPL * kGridBoxRows;
+  const int64_t r0 = tile * kTileRows;
+  // boxes holding full rows
+  const int nbox = r0 >= rows ? 0 : (int)min((int64_t)RPL, (rows - r0 + kGridBoxRows - 1) / kGridBoxRows);
   if (tid == 0 && nbox > 0) {
     mbar_arrive_expect_tx(&s_bar, (uint32_t)nbox * kGridBoxRows * 128u);
     for (int bx = 0; bx < nbox; ++bx)
       tma_load_2d(buf + bx * kGridBoxRows * 8, &tin, 0, (int)(r0 + bx * kGridBoxRows), &s_bar);
   }
-  // lane owns rows rl0 = 64w + lane and rl1 = rl0 + 32 of the tile
-  const int rl0 = warp * 64 + lane, rl1 = rl0 + 32;
+  // lane owns rows 32 * (RPL * w + j) + lane, j < RPL, of the tile
+  int rl[RPL];
+#pragma unroll
+  for (int j = 0; j < RPL; ++j) rl[j] = 32 * (RPL * warp + j) + lane;
   const uint32_t pad = to_bits(R::pad());
   if (nbox > 0) {
     const bool ok = mbar_wait_bounded(&s_bar, 0u, limit);
@@ -662,8 +677,8 @@ __global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ 
       buf[rl * 8 + (j ^ (rl & 7))] = q;
     }
   };
-  fill_partial(rl0);
-  fill_partial(rl1);
+#pragma unroll
+  for (int j = 0; j < RPL; ++j) fill_partial(rl[j]);
   // ---- pass A: row totals (left folds)
   auto row_total = [&](int rl) {
     V tot = R::ident();
@@ -685,13 +700,15 @@ __global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ 
     }
     return v;
   };
-  const V i0 = warp_incl(row_total(rl0));
-  const V t0 = R::shfl_idx(i0, 31, 32);
-  const V i1 = R::op(t0, warp_incl(row_total(rl1)));
-  const V e0 = R::shfl_up(i0, 1, 32), e1 = R::shfl_up(i1, 1, 32);
-  const V pre0 = lane == 0 ? R::ident() : e0;
-  const V pre1 = lane == 0 ? t0 : e1;
-  if (lane == 31) s_wtot[warp] = i1;
+  V pre[RPL], run = R::ident();  // run: the warp's earlier rows in all
+#pragma unroll
+  for (int j = 0; j < RPL; ++j) {
+    const V ij = R::op(run, warp_incl(row_total(rl[j])));
+    const V ej = R::shfl_up(ij, 1, 32);
+    pre[j] = lane == 0 ? run : ej;
+    run = R::shfl_idx(ij, 31, 32);
+  }
+  if (lane == 31) s_wtot[warp] = run;
   __syncthreads();
   if (warp == 0) {
     V total = R::ident();
@@ -741,8 +758,8 @@ __global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ 
     }
   };
   const V cw = s_cp[warp];
-  carry_row(rl0, R::op(cw, pre0));
-  carry_row(rl1, R::op(cw, pre1));
+#pragma unroll
+  for (int j = 0; j < RPL; ++j) carry_row(rl[j], R::op(cw, pre[j]));
   fence_proxy_async_smem();
   __syncthreads();
   if (tid == 0)
@@ -760,8 +777,8 @@ __global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ 
       if (e + 3 < n) out[e + 3] = q.w;
     }
   };
-  store_partial(rl0);
-  store_partial(rl1);
+#pragma unroll
+  for (int j = 0; j < RPL; ++j) store_partial(rl[j]);
   if (tid == 0 && nbox > 0) tma_store_wait_read();  // the boxes have left shared memory
 }
 
@@ -850,7 +867,9 @@ static cox_status launch_scan_scope(cox_scope scope, int block, const void* d_in
     return launch_status();
   }
   if (n >= 32 && n / 32 < (int64_t(1) << 31) && aligned16(d_in) && aligned16(d_out)) {
-    const int64_t ntiles = (n + kGridRowsTile * 32 - 1) / (kGridRowsTile * 32);
+    constexpr int RPL = grid_rows_rpl<R>();
+    constexpr int64_t kTileElems = (int64_t)RPL * kGridBoxRows * 32;
+    const int64_t ntiles = (n + kTileElems - 1) / kTileElems;
     const size_t need = scan_ws_bytes(ntiles) + 24 * (size_t)((ntiles + 31) / 32);  // + group words
     if (!ws || ws_bytes < need) return COX_ENOMEM;
     if (!aligned16(ws)) return COX_EINVAL;
@@ -859,13 +878,13 @@ static cox_status launch_scan_scope(cox_scope scope, int block, const void* d_in
       return COX_ECUDA;
     if (cudaMemsetAsync(ws, 0, need, st) != cudaSuccess) return COX_ECUDA;
     const ScanWs w = scan_ws(ws, ntiles);
-    auto k = k_scan_grid_rows<R>;
-    const size_t smem = (size_t)kGridRowsTile * 128 + 1024;
-    static bool attr = false;
-    if (!attr) {
+    auto k = k_scan_grid_rows<R, RPL>;
+    const size_t smem = (size_t)RPL * kGridBoxRows * 128 + 1024;
+    static bool attr[kMaxDevices];  // per device
+    if (!attr[device_index()]) {
       if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return COX_ECUDA;
-      attr = true;
+      attr[device_index()] = true;
     }
     k<<<(unsigned)ntiles, 256, smem, st>>>(tin, tout, in, out, n, w.ticket, w.flags, w.agg, w.inc, ntiles, excl,
                                            spin_limit(), device_status_word());
