@@ -27,6 +27,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstddef>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -95,22 +96,17 @@ inline size_t serve_smem(size_t nreq) { return (size_t)(kTile + kServeCounts + 4
 
 // ---------------------------------------------------------------- reduce
 // Thread t folds elements 1024 j + 4 t + k (j = 0..blocks-1, k = 0..3) of the
-// tile, in that order; elements past the request's end were loaded as 0.
+// tile, in that order; elements past the request's end count as 0.  The
+// tile's block sum goes to part[c] in the request's workspace; the tile that
+// completes the request folds the parts (thread t: parts t, t + 256, ...),
+// block-reduces them and writes the sum and its low word.  `ctr` counts the
+// request's finished tiles; the folding tile returns true.
 template <class R>
-__device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, const uint32_t* buf, int blocks, typename R::V* wpart,
-                                  unsigned* ctr) {
+__device__ bool reduce_tile_finish(const ReqDesc& d, int64_t c, typename R::V acc, typename R::V* wpart,
+                                   unsigned* ctr) {
   using T = typename R::T;
   using V = typename R::V;
   const int tid = threadIdx.x;
-  V acc = R::ident();
-#pragma unroll 4
-  for (int j = 0; j < blocks; ++j) {  // (the rest of a partial tile would only add the identity)
-    const uint4 q = *reinterpret_cast<const uint4*>(buf + j * 4 * kServeBlock + 4 * tid);
-    acc = R::op(acc, R::load(from_bits<T>(q.x)));
-    acc = R::op(acc, R::load(from_bits<T>(q.y)));
-    acc = R::op(acc, R::load(from_bits<T>(q.z)));
-    acc = R::op(acc, R::load(from_bits<T>(q.w)));
-  }
   const V bsum = block_reduce32<R>(acc, wpart);
   V* part = reinterpret_cast<V*>(d.ws);
   __shared__ int s_last;
@@ -120,7 +116,7 @@ __device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, const uint32_t* b
     s_last = d.nitems == 1 || atomicAdd(ctr, 1u) == (unsigned)(d.nitems - 1);
   }
   __syncthreads();
-  if (!s_last) return;
+  if (!s_last) return false;
   __threadfence();
   V fold = R::ident();
   for (int64_t k = tid; k < d.nitems; k += kServeBlock) {
@@ -138,6 +134,64 @@ __device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, const uint32_t* b
     d.out[0] = to_bits(R::out(total));
     d.out[1] = __float_as_uint(R::lo(total));
   }
+  return true;
+}
+
+// The fold of a tile staged in shared memory (the batch kernel).
+template <class R>
+__device__ void serve_reduce_tile(const ReqDesc& d, int64_t c, const uint32_t* buf, int blocks, typename R::V* wpart,
+                                  unsigned* ctr) {
+  using T = typename R::T;
+  using V = typename R::V;
+  const int tid = threadIdx.x;
+  V acc = R::ident();
+#pragma unroll 4
+  for (int j = 0; j < blocks; ++j) {  // (the rest of a partial tile would only add the identity)
+    const uint4 q = *reinterpret_cast<const uint4*>(buf + j * 4 * kServeBlock + 4 * tid);
+    acc = R::op(acc, R::load(from_bits<T>(q.x)));
+    acc = R::op(acc, R::load(from_bits<T>(q.y)));
+    acc = R::op(acc, R::load(from_bits<T>(q.z)));
+    acc = R::op(acc, R::load(from_bits<T>(q.w)));
+  }
+  reduce_tile_finish<R>(d, c, acc, wpart, ctr);
+}
+
+// A lone reduce request (a batch of one): one CTA per tile reads its tile
+// straight from global memory in the batch kernel's element order, so the
+// sum is the batch kernel's bit for bit, without its tile counter, request
+// flags or exit count; the slot's event tells the host it is done.  `ctr`
+// is the slot's reduce counter for request 0 (zero between launches; the
+// folding CTA zeroes it again).
+template <class R>
+__global__ void __launch_bounds__(kServeBlock) k_serve_reduce_solo(const ReqDesc d, unsigned* ctr) {
+  using T = typename R::T;
+  using V = typename R::V;
+  __shared__ V wpart[32];
+  const int tid = threadIdx.x;
+  const int64_t c = blockIdx.x, base = c * kTile;
+  const int valid = (int)min(kTile, d.n - base);
+  const int blocks = (valid + 1023) / 1024;
+  const uint32_t* src = d.in + base;
+  const bool vec = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+  V acc = R::ident();
+#pragma unroll 4
+  for (int j = 0; j < blocks; ++j) {
+    const int e = j * 4 * kServeBlock + 4 * tid;
+    uint4 q;
+    if (vec && e + 4 <= valid) {
+      q = __ldcs(reinterpret_cast<const uint4*>(src + e));
+    } else {
+      q.x = e < valid ? src[e] : 0u;
+      q.y = e + 1 < valid ? src[e + 1] : 0u;
+      q.z = e + 2 < valid ? src[e + 2] : 0u;
+      q.w = e + 3 < valid ? src[e + 3] : 0u;
+    }
+    acc = R::op(acc, R::load(from_bits<T>(q.x)));
+    acc = R::op(acc, R::load(from_bits<T>(q.y)));
+    acc = R::op(acc, R::load(from_bits<T>(q.z)));
+    acc = R::op(acc, R::load(from_bits<T>(q.w)));
+  }
+  if (reduce_tile_finish<R>(d, c, acc, wpart, ctr) && tid == 0) *ctr = 0u;
 }
 
 // ------------------------------------------------------------------ scan
@@ -558,8 +612,8 @@ struct cox_server {
   // Enqueues a filled batch on the slot's stream (without `mu`: submitters
   // are not held up by the launch calls).
   // A batch of one scan or compaction runs the op's own kernel (cox_tile_scan,
-  // cox_ballot_compact): the same results bit for bit, at the latency of one
-  // launch per request.  Other small batches pass their table as a kernel
+  // cox_ballot_compact), and a lone reduce k_serve_reduce_solo: the same
+  // results bit for bit, at the latency of one launch per request.  Other small batches pass their table as a kernel
   // parameter; larger ones copy it to the slot's device table first.
   bool issue_batch(Slot& sl, size_t tab_bytes, int64_t items, bool has_compact) {
     const int nreq = reinterpret_cast<BatchHdr*>(sl.host_tab)->nreq;
@@ -573,10 +627,19 @@ struct cox_server {
         c = cox_ballot_compact((cox_dtype)d.dt, 32, 256, d.in, d.n, d.threshold, d.out,
                                reinterpret_cast<int64_t*>(d.ws), d.ws + kAlign, wsb, 0u, sl.st);
       }
-      if (d.kind != COX_REQ_REDUCE) {
-        sl.solo = true;
-        return c == COX_OK && cudaEventRecord(sl.ev, sl.st) == cudaSuccess;
+      if (d.kind == COX_REQ_REDUCE) {
+        const unsigned nblk = (unsigned)d.nitems;
+        unsigned* rc = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(sl.ctr) + offsetof(SlotCtr, red));
+        if (d.dt == COX_F32 && (d.flags & COX_F_COMPENSATED))
+          k_serve_reduce_solo<Comp><<<nblk, kServeBlock, 0, sl.st>>>(d, rc);
+        else if (d.dt == COX_F32)
+          k_serve_reduce_solo<Plain<AddF>><<<nblk, kServeBlock, 0, sl.st>>>(d, rc);
+        else
+          k_serve_reduce_solo<Plain<AddU>><<<nblk, kServeBlock, 0, sl.st>>>(d, rc);
+        c = cudaGetLastError() == cudaSuccess ? COX_OK : COX_ECUDA;
       }
+      sl.solo = true;
+      return c == COX_OK && cudaEventRecord(sl.ev, sl.st) == cudaSuccess;
     }
     sl.solo = false;
     has_compact = has_compact && items > 1;  // (a lone tile's look-back reads no descriptor)

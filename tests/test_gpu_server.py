@@ -89,6 +89,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix(cox):
             srv.release(t)
         st = srv.stats()
         assert st["completed"] == len(mix) and st["failed"] == 0
+        assert st["max_batch"] > 1  # the mix shared launches; each request below runs alone
         for (r, d, h), got in zip(mix, in_mix):
             t = srv.submit(r, keep=d)
             srv.wait(t)
@@ -145,9 +146,10 @@ def test_full_size_mix_against_the_oracle(cox):
 
 def test_requests_one_at_a_time_match_the_oracle(cox):
     """An idle server launches each request from the submitting thread (a lone
-    scan or compaction with the op's own kernel); a request must not be marked
-    done before its results are in memory, so every result read right after
-    the wait must match the oracle."""
+    scan or compaction with the op's own kernel, a lone reduce with one CTA
+    per tile in the batch kernel's order); a request must not be marked done
+    before its results are in memory, so every result read right after the
+    wait must match the oracle."""
     mix = make_mix(cox, 36, seed=51, lo=1000, hi=1 << 20)
     srv = cox.Server(1 << 30)
     try:
