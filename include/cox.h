@@ -553,6 +553,10 @@ typedef struct {
  * soon as the kernel raises that request's flag in pinned host memory --
  * after its last tile's results are in device memory, without waiting for
  * the rest of the batch -- or at the latest when the batch's event fires.
+ * A batch of one request runs that op's own kernel instead (a scan or
+ * compaction: cox_tile_scan or cox_ballot_compact; a reduce: one CTA per
+ * tile in the batch kernel's order) and completes with its event, so an
+ * idle server costs one launch per request.
  * Each request's arithmetic depends only on the request (its tiles, its
  * fixed-order combine), never on what else shares its launch.
  */
