@@ -557,6 +557,7 @@ struct cox_server {
   int64_t ready_items = 0;  // tiles of the admitted, not yet launched requests
   std::unordered_map<uint64_t, SReq> reqs;
   std::vector<std::pair<uint64_t, double>> finished;  // (ticket, t_done) for trace runners
+  std::atomic<int64_t> nfinished{0};                   // entries added to `finished`, ever
   bool collect_finished = false;
   Slot slots[kSlots];
   std::thread thr;
@@ -668,7 +669,10 @@ struct cox_server {
     if (it == reqs.end()) return;
     it->second.state = state;
     it->second.t_done = t;
-    if (collect_finished) finished.emplace_back(sl.tickets[i], t);
+    if (collect_finished) {
+      finished.emplace_back(sl.tickets[i], t);
+      nfinished.fetch_add(1, std::memory_order_release);
+    }
     if (state == kDone) {
       stats.completed += 1;
       stats.wait_s += it->second.t_launch - it->second.t_submit;
@@ -983,6 +987,7 @@ extern "C" cox_status cox_server_run_trace(cox_server* s, const cox_trace_item* 
   int64_t next = 0, done = 0;
   cox_status rc = COX_OK;
   std::vector<std::pair<uint64_t, double>> fin;
+  int64_t seen = s->nfinished.load();
   double last = t0;
   while (done < count) {
     const double t = now_s() - t0;
@@ -998,9 +1003,12 @@ extern "C" cox_status cox_server_run_trace(cox_server* s, const cox_trace_item* 
       }
       ++next;
     }
-    {
+    // (the lock only when the scheduler has added entries since the last look)
+    const int64_t nf = s->nfinished.load(std::memory_order_acquire);
+    if (nf != seen) {
       std::lock_guard<std::mutex> g(s->mu);
       fin.swap(s->finished);
+      seen = nf;
     }
     for (auto& f : fin) {
       auto it = index.find(f.first);
