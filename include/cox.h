@@ -565,6 +565,12 @@ cox_status cox_server_create(size_t budget_bytes, int max_requests, cox_server**
 /* Queues a request; COX_ENOMEM if it could never fit the budget. */
 cox_status cox_server_submit(cox_server* s, const cox_request* req, uint64_t* ticket);
 
+/* Queues count requests at once (tickets[i] for reqs[i]), so that the
+ * scheduler sees them together and, load permitting, packs them into one
+ * launch.  All are checked first: on an error (COX_EINVAL, COX_ENOMEM as for
+ * cox_server_submit) none is queued. */
+cox_status cox_server_submit_many(cox_server* s, const cox_request* reqs, int64_t count, uint64_t* tickets);
+
 /* *done = 1 once the request's results are on the device. */
 cox_status cox_server_poll(cox_server* s, uint64_t ticket, int* done);
 

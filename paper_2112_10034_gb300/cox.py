@@ -68,6 +68,7 @@ SIGNATURES = {
     "cox_batch_tune_lookup": (_I, [ctypes.c_char_p, _I64, _I64, _P]),
     "cox_server_create": (_I, [_SZ, _I, _P]),
     "cox_server_submit": (_I, [_P, _P, _P]),
+    "cox_server_submit_many": (_I, [_P, _P, _I64, _P]),
     "cox_server_poll": (_I, [_P, ctypes.c_uint64, _P]),
     "cox_server_wait": (_I, [_P, ctypes.c_uint64, ctypes.c_double]),
     "cox_server_result": (_I, [_P, ctypes.c_uint64, _P, _P]),
@@ -553,6 +554,17 @@ class Server:
         if keep is not None:
             self._keep[t.value] = keep
         return t.value
+
+    def submit_many(self, reqs, keep=None) -> list:
+        """Queues the requests together (cox_server_submit_many); keep[i] is
+        held for reqs[i] until it is released."""
+        arr = (cox_request * len(reqs))(*reqs)
+        ts = (ctypes.c_uint64 * len(reqs))()
+        _check(lib().cox_server_submit_many(self.handle, arr, len(reqs), ts), "cox_server_submit_many")
+        if keep is not None:
+            for t, k in zip(ts, keep):
+                self._keep[t] = k
+        return list(ts)
 
     def poll(self, ticket: int) -> bool:
         d = ctypes.c_int()

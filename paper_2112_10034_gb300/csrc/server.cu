@@ -3,11 +3,15 @@
 // Host side.  A device arena of `budget` bytes holds every admitted
 // request's output and workspace; a scheduler thread admits queued requests
 // in arrival order while the arena and the slot count allow, packs all
-// admitted, not yet launched requests into one persistent launch on one of
-// kSlots streams (so a batch launched while an earlier one runs overlaps it
-// on the device), and marks each request done when the kernel raises the
-// request's flag in pinned host memory (after the request's last tile), or
-// at the latest when the batch's event fires.
+// admitted, not yet launched requests into one persistent launch on its
+// slot's stream (so a batch launched while an earlier one runs overlaps it
+// on the device; at most kBatchSlots such batches at a time), and marks each
+// request done when the kernel raises the request's flag in pinned host
+// memory (after the request's last tile), or at the latest when the batch's
+// event fires.  At low load (only lone requests in flight, a short queue)
+// every request goes out alone as soon as it arrives, with its op's own
+// kernel on one stream shared by all slots, in order, and completes with
+// its slot's event: one launch per request, as without the server.
 //
 // Device side.  A batch is a table of request descriptors; each request is
 // cut into tiles of kTile = 16384 elements (64 KB), numbered consecutively
@@ -43,7 +47,8 @@ namespace cox {
 
 constexpr int kServeBlock = 256;
 constexpr int64_t kTile = kBigTile;  // 16384 elements per tile
-constexpr int kSlots = 3;            // batches in flight
+constexpr int kSlots = 8;            // launches in flight (lone requests or batches)
+constexpr int kBatchSlots = 3;       // batches of several requests in flight
 constexpr int kMaxBatch = 2048;      // requests per launch
 constexpr size_t kAlign = 256;
 
@@ -515,6 +520,7 @@ struct SReq {
 // until they fill the persistent grid with tiles or the oldest has waited
 // this long: fewer, larger batches under load, no added wait at low load.
 constexpr double kBatchDelay = 20e-6;
+constexpr size_t kSoloQueue = 2;  // ready requests at most, at low load, that each run alone
 constexpr double kEventPoll = 100e-6;  // how often a running batch's event is queried
 
 struct Slot {
@@ -532,6 +538,7 @@ struct Slot {
   // thread than the completion checks).
   std::atomic<bool> issued{false};
   bool solo = false;         // the batch ran as one op's own kernel (no flags: its event tells)
+  cudaStream_t launched = nullptr;  // the stream the slot's work last went to
   double t_checked = 0.0;    // when the slot's event was last queried
   std::vector<uint64_t> tickets;
   std::vector<char> marked;  // requests of the batch already marked done
@@ -558,6 +565,9 @@ struct cox_server {
   std::unordered_map<uint64_t, SReq> reqs;
   std::vector<std::pair<uint64_t, double>> finished;  // (ticket, t_done) for trace runners
   std::atomic<int64_t> nfinished{0};                   // entries added to `finished`, ever
+  // Lone requests of every slot go to one stream, in launch order, as one
+  // launch per request would; batches of several run on their slot's stream.
+  cudaStream_t solo_st = nullptr;
   bool collect_finished = false;
   Slot slots[kSlots];
   std::thread thr;
@@ -622,27 +632,29 @@ struct cox_server {
       const ReqDesc& d = *reinterpret_cast<const ReqDesc*>(sl.host_tab + sizeof(BatchHdr));
       cox_status c = COX_EINVAL;
       if (d.kind == COX_REQ_SCAN) {
-        c = cox_tile_scan(COX_SUM, (cox_dtype)d.dt, d.width, 256, d.in, d.out, d.n, d.flags, sl.st);
+        c = cox_tile_scan(COX_SUM, (cox_dtype)d.dt, d.width, 256, d.in, d.out, d.n, d.flags, solo_st);
       } else if (d.kind == COX_REQ_COMPACT) {
         const size_t wsb = cox_ballot_compact_workspace(d.n, 256);
         c = cox_ballot_compact((cox_dtype)d.dt, 32, 256, d.in, d.n, d.threshold, d.out,
-                               reinterpret_cast<int64_t*>(d.ws), d.ws + kAlign, wsb, 0u, sl.st);
+                               reinterpret_cast<int64_t*>(d.ws), d.ws + kAlign, wsb, 0u, solo_st);
       }
       if (d.kind == COX_REQ_REDUCE) {
         const unsigned nblk = (unsigned)d.nitems;
         unsigned* rc = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(sl.ctr) + offsetof(SlotCtr, red));
         if (d.dt == COX_F32 && (d.flags & COX_F_COMPENSATED))
-          k_serve_reduce_solo<Comp><<<nblk, kServeBlock, 0, sl.st>>>(d, rc);
+          k_serve_reduce_solo<Comp><<<nblk, kServeBlock, 0, solo_st>>>(d, rc);
         else if (d.dt == COX_F32)
-          k_serve_reduce_solo<Plain<AddF>><<<nblk, kServeBlock, 0, sl.st>>>(d, rc);
+          k_serve_reduce_solo<Plain<AddF>><<<nblk, kServeBlock, 0, solo_st>>>(d, rc);
         else
-          k_serve_reduce_solo<Plain<AddU>><<<nblk, kServeBlock, 0, sl.st>>>(d, rc);
+          k_serve_reduce_solo<Plain<AddU>><<<nblk, kServeBlock, 0, solo_st>>>(d, rc);
         c = cudaGetLastError() == cudaSuccess ? COX_OK : COX_ECUDA;
       }
       sl.solo = true;
-      return c == COX_OK && cudaEventRecord(sl.ev, sl.st) == cudaSuccess;
+      sl.launched = solo_st;
+      return c == COX_OK && cudaEventRecord(sl.ev, solo_st) == cudaSuccess;
     }
     sl.solo = false;
+    sl.launched = sl.st;
     has_compact = has_compact && items > 1;  // (a lone tile's look-back reads no descriptor)
     const int g = (int)std::min<int64_t>(grid, items);
     const size_t smem = serve_smem((size_t)nreq);
@@ -701,17 +713,24 @@ struct cox_server {
       ready.push_back(queue.front());
       queue.pop_front();
     }
-    int inflight = 0;
-    for (const Slot& sl : slots) inflight += sl.busy;
-    // Launch at once while at most one batch runs; with more in flight, hold
-    // the admitted requests back until they fill the grid or the oldest has
-    // waited kBatchDelay: fewer, larger batches under load.
-    const bool go = !ready.empty() && inflight < kSlots &&
-                    (inflight <= 1 || ready_items >= grid || now - reqs[ready.front()].t_ready >= kBatchDelay);
-    if (!go) return nullptr;
+    int inflight = 0, batches = 0;  // busy slots; those running several requests
+    for (const Slot& sl : slots) {
+      inflight += sl.busy;
+      batches += sl.busy && sl.tickets.size() > 1;
+    }
+    // Low load (only lone requests in flight, at most kSoloQueue ready): the
+    // oldest ready request goes out alone at once.  Otherwise all ready
+    // requests go out as one batch while at most one slot is busy, or once
+    // they fill the grid or the oldest has waited kBatchDelay: fewer, larger
+    // batches under load.
+    if (ready.empty() || inflight >= kSlots) return nullptr;
+    const bool solo_now = batches == 0 && ready.size() <= kSoloQueue;
+    const bool batch_go = batches < kBatchSlots && (inflight <= 1 || ready_items >= grid ||
+                                                    now - reqs[ready.front()].t_ready >= kBatchDelay);
+    if (!solo_now && !batch_go) return nullptr;
     for (Slot& sl : slots) {
       if (sl.busy) continue;
-      const size_t k = std::min<size_t>(ready.size(), kMaxBatch);
+      const size_t k = solo_now ? 1 : std::min<size_t>(ready.size(), kMaxBatch);
       std::vector<uint64_t> ts(ready.begin(), ready.begin() + k);
       ready.erase(ready.begin(), ready.begin() + k);
       *tab_bytes = fill_batch(sl, ts, items, has_compact);
@@ -728,7 +747,7 @@ struct cox_server {
       return;
     }
     // What did get enqueued ends before the slot's table is written again.
-    cudaStreamSynchronize(sl->st);
+    cudaStreamSynchronize(sl->launched ? sl->launched : sl->st);
     std::lock_guard<std::mutex> g(mu);
     for (size_t i = 0; i < sl->tickets.size(); ++i) mark_done(*sl, i, kFailed, now_s());
     sl->tickets.clear();
@@ -807,6 +826,10 @@ extern "C" cox_status cox_server_create(size_t budget_bytes, int max_requests, c
     return COX_ENOMEM;
   }
   s->arena = new Arena(s->budget);
+  if (cudaStreamCreateWithFlags(&s->solo_st, cudaStreamNonBlocking) != cudaSuccess) {
+    cox_server_destroy(s);
+    return COX_ECUDA;
+  }
   const size_t tab = table_bytes(kMaxBatch);
   for (Slot& sl : s->slots) {
     if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
@@ -838,39 +861,70 @@ extern "C" cox_status cox_server_create(size_t budget_bytes, int max_requests, c
   return COX_OK;
 }
 
-extern "C" cox_status cox_server_submit(cox_server* s, const cox_request* req, uint64_t* ticket) {
-  if (!s || !req || !ticket) return COX_EINVAL;
-  const cox_status c = check_request(*req);
+namespace {
+
+// A request's host record: validated, its arena bytes computed.
+cox_status make_sreq(const cox_server* s, const cox_request& req, SReq* q) {
+  const cox_status c = check_request(req);
   if (c != COX_OK) return c;
-  SReq q;
-  q.r = *req;
-  q.t_submit = now_s();
+  q->r = req;
+  q->t_submit = now_s();
   size_t ob, wb;
-  request_bytes(*req, &ob, &wb);
-  q.out_b = ob;
-  q.bytes = ob + wb;
-  q.held = q.bytes + round_up((size_t)req->n * 4);  // input counted as held while in flight
-  if (q.bytes > s->budget || q.held > s->budget) return COX_ENOMEM;
+  request_bytes(req, &ob, &wb);
+  q->out_b = ob;
+  q->bytes = ob + wb;
+  q->held = q->bytes + round_up((size_t)req.n * 4);  // input counted as held while in flight
+  if (q->bytes > s->budget || q->held > s->budget) return COX_ENOMEM;
+  return COX_OK;
+}
+
+// Queues count validated requests under one lock.  An idle server (nothing
+// queued, ready or running) plans and launches them from the submitting
+// thread when the server's device is current there, without waiting for the
+// scheduler thread to notice them.
+void enqueue(cox_server* s, SReq* qs, int64_t count, uint64_t* tickets) {
   Slot* launch = nullptr;
   size_t tab_bytes = 0;
   int64_t items = 0;
   bool has_compact = false;
   {
     std::lock_guard<std::mutex> g(s->mu);
-    const uint64_t t = s->next_ticket++;
-    s->reqs.emplace(t, q);
-    s->queue.push_back(t);
-    s->stats.submitted += 1;
-    *ticket = t;
-    // An idle server launches from the submitting thread (when the server's
-    // device is current there), without waiting for the scheduler thread to
-    // notice the request.
-    int cur = -1;
-    bool idle = s->queue.size() == 1 && s->ready.empty() && cudaGetDevice(&cur) == cudaSuccess && cur == s->dev;
+    bool idle = s->queue.empty() && s->ready.empty();
     for (const Slot& sl : s->slots) idle = idle && !sl.busy;
-    if (idle) launch = s->plan_launch(&tab_bytes, &items, &has_compact);
+    for (int64_t i = 0; i < count; ++i) {
+      const uint64_t t = s->next_ticket++;
+      s->reqs.emplace(t, qs[i]);
+      s->queue.push_back(t);
+      s->stats.submitted += 1;
+      tickets[i] = t;
+    }
+    int cur = -1;
+    if (idle && cudaGetDevice(&cur) == cudaSuccess && cur == s->dev)
+      launch = s->plan_launch(&tab_bytes, &items, &has_compact);
   }
   if (launch) s->launch_planned(launch, tab_bytes, items, has_compact);
+}
+
+}  // namespace
+
+extern "C" cox_status cox_server_submit(cox_server* s, const cox_request* req, uint64_t* ticket) {
+  if (!s || !req || !ticket) return COX_EINVAL;
+  SReq q;
+  const cox_status c = make_sreq(s, *req, &q);
+  if (c != COX_OK) return c;
+  enqueue(s, &q, 1, ticket);
+  return COX_OK;
+}
+
+extern "C" cox_status cox_server_submit_many(cox_server* s, const cox_request* reqs, int64_t count,
+                                             uint64_t* tickets) {
+  if (!s || count < 0 || (count > 0 && (!reqs || !tickets))) return COX_EINVAL;
+  std::vector<SReq> qs((size_t)count);
+  for (int64_t i = 0; i < count; ++i) {
+    const cox_status c = make_sreq(s, reqs[i], &qs[(size_t)i]);
+    if (c != COX_OK) return c;
+  }
+  if (count > 0) enqueue(s, qs.data(), count, tickets);
   return COX_OK;
 }
 
@@ -958,6 +1012,10 @@ extern "C" void cox_server_destroy(cox_server* s) {
     }
     s->stop.store(true);
     s->thr.join();
+  }
+  if (s->solo_st) {
+    cudaStreamSynchronize(s->solo_st);
+    cudaStreamDestroy(s->solo_st);
   }
   for (Slot& sl : s->slots) {
     if (sl.st) cudaStreamSynchronize(sl.st);

@@ -81,7 +81,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix(cox):
     mix = make_mix(cox, 45, seed=11)
     srv = cox.Server(1 << 30)
     try:
-        tickets = [srv.submit(r, keep=d) for r, d, _ in mix]
+        tickets = srv.submit_many([r for r, _, _ in mix], keep=[d for _, d, _ in mix])
         for t in tickets:
             srv.wait(t)
         in_mix = [srv.result(t, r) for t, (r, _, _) in zip(tickets, mix)]
@@ -89,7 +89,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix(cox):
             srv.release(t)
         st = srv.stats()
         assert st["completed"] == len(mix) and st["failed"] == 0
-        assert st["max_batch"] > 1  # the mix shared launches; each request below runs alone
+        assert st["max_batch"] == len(mix)  # queued together: one launch; each request below runs alone
         for (r, d, h), got in zip(mix, in_mix):
             t = srv.submit(r, keep=d)
             srv.wait(t)
@@ -106,9 +106,9 @@ def test_each_result_is_the_same_alone_and_in_the_mix(cox):
 def test_full_size_mix_against_the_oracle(cox):
     """Twenty requests of the serving workload's kinds with sizes up to 16M
     elements (several at exactly 2^24, so large requests take many tiles and
-    deep look-backs inside one persistent launch), all submitted before any
-    completes so they share launches; every result must match the oracle and
-    the same request run alone."""
+    deep look-backs inside one persistent launch), queued together so they
+    share launches; every result must match the oracle and the same request
+    run alone."""
     count = 20
     mix = make_mix(cox, count, seed=31, lo=1024, hi=1 << 24)
     import torch
@@ -124,7 +124,7 @@ def test_full_size_mix_against_the_oracle(cox):
     assert max(r.n for r, _, _ in mix) == 1 << 24
     srv = cox.Server(6 << 30)
     try:
-        tickets = [srv.submit(r, keep=d) for r, d, _ in mix]
+        tickets = srv.submit_many([r for r, _, _ in mix], keep=[d for _, d, _ in mix])
         for t in tickets:
             srv.wait(t, timeout_s=120.0)
         in_mix = [srv.result(t, r) for t, (r, _, _) in zip(tickets, mix)]
@@ -132,6 +132,7 @@ def test_full_size_mix_against_the_oracle(cox):
             srv.release(t)
         st = srv.stats()
         assert st["completed"] == len(mix) and st["failed"] == 0
+        assert st["max_batch"] > 1
         for (r, d, h), got in zip(mix, in_mix):
             check_against_oracle(cox, r, h, got)
             t = srv.submit(r, keep=d)
@@ -214,5 +215,9 @@ def test_bad_requests_are_rejected(cox):
         r = cox.make_request(cox.COX_REQ_REDUCE, x.view(torch.int32), compensated=True)
         with pytest.raises(cox.CoxError):
             srv.submit(r)
+        good = cox.make_request(cox.COX_REQ_REDUCE, x)
+        with pytest.raises(cox.CoxError):  # one bad request: none of the group is queued
+            srv.submit_many([good, r, good])
+        assert srv.stats()["submitted"] == 0
     finally:
         srv.close()
