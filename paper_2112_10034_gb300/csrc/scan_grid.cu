@@ -583,6 +583,21 @@ __global__ void __launch_bounds__(256) k_scan_grid(const uint32_t* __restrict__ 
 // row (n % 32 elements) is read and written by its lane from global memory.
 constexpr int kGridBoxRows = 256;  // rows per TMA box; a tile is RPL boxes (RPL rows per lane)
 
+// a op x for one element x: for a compensated pair the element's error word
+// is zero, so the error words need one add (a.e + t), not two.
+template <class R>
+__device__ __forceinline__ typename R::V op_elem(typename R::V a, typename R::T x) {
+  if constexpr (R::kComp) {
+    Pair r;
+    float t;
+    two_sum(a.s, x, r.s, t);
+    r.e = __fadd_rn(a.e, t);
+    return r;
+  } else {
+    return R::op(a, R::load(x));
+  }
+}
+
 template <class R, int RPL>
 __global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ CUtensorMap tin,
                                                         const __grid_constant__ CUtensorMap tout,
@@ -685,10 +700,10 @@ __global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ 
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const uint4 q = buf[rl * 8 + (j ^ (rl & 7))];
-      tot = R::op(tot, R::load(from_bits<T>(q.x)));
-      tot = R::op(tot, R::load(from_bits<T>(q.y)));
-      tot = R::op(tot, R::load(from_bits<T>(q.z)));
-      tot = R::op(tot, R::load(from_bits<T>(q.w)));
+      tot = op_elem<R>(tot, from_bits<T>(q.x));
+      tot = op_elem<R>(tot, from_bits<T>(q.y));
+      tot = op_elem<R>(tot, from_bits<T>(q.z));
+      tot = op_elem<R>(tot, from_bits<T>(q.w));
     }
     return tot;
   };
@@ -750,7 +765,7 @@ __global__ void __launch_bounds__(256) k_scan_grid_rows(const __grid_constant__ 
       uint32_t* w = &q.x;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const V nx = R::op(carry, R::load(from_bits<T>(w[k])));
+        const V nx = op_elem<R>(carry, from_bits<T>(w[k]));
         w[k] = to_bits(R::out(excl ? carry : nx));
         carry = nx;
       }
