@@ -685,33 +685,35 @@ __global__ void __launch_bounds__(96 * StripCfg<DT>::NP, 1)
     // -------------------------------------------------- left-sum warp
     team_sync(team);
     const int r = lane % RB, h = lane / RB;  // row and part of the row
-    uint64_t wa[kClGroup], wb[kClGroup];  // first words of the next two jobs, loaded ahead
-    // Row r's left-strip words, part h: strips h, h + HL, ... below s.
-    auto cl_base = [&](const StripJob& jb, int64_t& cnt) {
+    // A job's row r, part h: its left-strip words (strips h, h + HL, ...
+    // below s; cnt of them from p on, stride apart) and the first group of
+    // them, loaded two jobs ahead.
+    struct Pre {
+      const unsigned long long* p;
+      int cnt;
+      uint64_t w[kClGroup];
+    };
+    Pre pa, pb;
+    const int64_t stride = (int64_t)HL * height;
+    auto prefetch = [&](const StripJob& jb, Pre& pr) {
       const int64_t y = (int64_t)jb.i * RB + r;
-      cnt = (y < height && jb.s > h) ? (jb.s - h + HL - 1) / HL : 0;
-      return A + (jb.g - jb.s + h) * height + y;
+      pr.cnt = (jb.q < njobs && y < height && jb.s > h) ? (int)((jb.s - h + HL - 1) / HL) : 0;
+      pr.p = A + (jb.g - jb.s + h) * height + y;
+      load_tagged(pr.p, stride, 0, min(pr.cnt, kClGroup), pr.w);
     };
-    auto prefetch = [&](const StripJob& jb, uint64_t (&w)[kClGroup]) {
-      int64_t cnt;
-      const unsigned long long* p = cl_base(jb, cnt);
-      load_tagged(p, HL * height, 0, jb.q < njobs ? min(cnt, (int64_t)kClGroup) : 0, w);
-    };
-    StripJob jp(sc, nsw), j2(sc, nsw);  // current, two ahead
-    // Left sum of job jp from its prefetched words w, then added into the
-    // slot's transpose; false on timeout.
-    auto step = [&](const uint64_t (&w)[kClGroup]) {
-      const int k = (int)(jp.q % NS);
-      if (!__all_sync(kFull, mbar_wait_bounded(tot + k, (uint32_t)((jp.q / NS) & 1), limit))) return false;
-      int64_t cnt;
-      const unsigned long long* p = cl_base(jp, cnt);
+    int k = 0;         // the current job's slot
+    uint32_t par = 0;  // and the parity of its use
+    // Left sum of the current job from its prefetched words, then added into
+    // the slot's transpose; false on timeout.
+    auto step = [&](const Pre& pr) {
+      if (!__all_sync(kFull, mbar_wait_bounded(tot + k, par, limit))) return false;
       uint32_t cl = 0;
-      bool good = add_tagged(p, HL * height, 0, min(cnt, (int64_t)kClGroup), w, limit, &cl);
-      for (int64_t j0 = kClGroup; good && j0 < cnt; j0 += kClGroup) {
-        const int64_t j1 = min(cnt, j0 + kClGroup);
+      bool good = add_tagged(pr.p, stride, 0, min(pr.cnt, kClGroup), pr.w, limit, &cl);
+      for (int j0 = kClGroup; good && j0 < pr.cnt; j0 += kClGroup) {
+        const int j1 = min(pr.cnt, j0 + kClGroup);
         uint64_t w2[kClGroup];
-        load_tagged(p, HL * height, j0, j1, w2);
-        good = add_tagged(p, HL * height, j0, j1, w2, limit, &cl);
+        load_tagged(pr.p, stride, j0, j1, w2);
+        good = add_tagged(pr.p, stride, j0, j1, w2, limit, &cl);
       }
       if (!__all_sync(kFull, good)) return false;
 #pragma unroll
@@ -723,26 +725,29 @@ __global__ void __launch_bounds__(96 * StripCfg<DT>::NP, 1)
       for (int t = 0; t < L; ++t) sr[t * SBP] += cl;
       __syncwarp();
       if (lane == 0) mbar_arrive(ready + k);
+      if (++k == NS) {
+        k = 0;
+        par ^= 1u;
+      }
       return true;
     };
-    prefetch(j2, wa);
+    StripJob j2(sc, nsw);  // the job two ahead of the current one
+    prefetch(j2, pa);
     j2.next(nst, sc, nsw);
-    prefetch(j2, wb);
+    prefetch(j2, pb);
     j2.next(nst, sc, nsw);
     bool ok = true;
-    // Jobs alternate between the two word buffers, each refilled with the
-    // job two ahead as soon as its own job is done.
-    while (jp.q < njobs) {
-      ok = step(wa);
+    // Jobs alternate between the two prefetch buffers, each refilled with
+    // the job two ahead as soon as its own job is done.
+    for (int64_t q = 0; q < njobs; q += 2) {
+      ok = step(pa);
       if (!ok) break;
-      prefetch(j2, wa);
-      jp.next(nst, sc, nsw);
+      prefetch(j2, pa);
       j2.next(nst, sc, nsw);
-      if (jp.q >= njobs) break;
-      ok = step(wb);
+      if (q + 1 >= njobs) break;
+      ok = step(pb);
       if (!ok) break;
-      prefetch(j2, wb);
-      jp.next(nst, sc, nsw);
+      prefetch(j2, pb);
       j2.next(nst, sc, nsw);
     }
     if (!ok && lane == 0) atomicOr(status, kDevTimeout);
