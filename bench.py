@@ -388,6 +388,22 @@ def run_secondary(dev, st):
     res["tile_scan_2p26_fp32_shuffle_form"] = sf
     del f1, y1
 
+    # the warp functions themselves (cox_shfl) on 2^26 int32 elements: one result per lane
+    # (4 bytes in + 4 out per element); shuffles at offset 1 / source lane 5, votes on
+    # values in [0, 15] (nonzero 15 times in 16), match_any over those 16 keys
+    ki = torch.from_numpy(inputs.uniform_int32(n, 0, 15, inputs.BASE_SEED + 6)).to(dev)
+    ko = torch.empty(n, dtype=torch.int32, device=dev)
+    wf = {}
+    for name, fn, param in (("shfl_idx", 0, 5), ("shfl_up", 1, 1), ("shfl_down", 2, 1), ("shfl_xor", 3, 1),
+                            ("ballot", 4, 0), ("any", 5, 0), ("all", 6, 0), ("match_any", 7, 0)):
+        for w in (32, 8):
+            ms = _time_launches(st, lambda: chk(cox.cox_shfl(fn, 0, w, BLOCK, ki.data_ptr(), ko.data_ptr(), n, param,
+                                                             cox.FULL_MASK, sh)))
+            gbs = n * 8 / (ms * 1e-3) / 1e9
+            wf[f"{name}_W{w}"] = {"us": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 3)}
+    res["warp_functions_2p26_int32"] = wf
+    del ki, ko
+
     # tile reduce of 2^26 fp32 (one result per tile; compensated with its low word)
     tr = {}
     for W in (2, 32):
