@@ -24,12 +24,22 @@ __global__ void __launch_bounds__(1024) k_shfl(const uint32_t* __restrict__ in, 
   const int seg = lane & ~(W - 1);
   const unsigned tbits = W == 32 ? kFull : ((1u << W) - 1u);
   const int64_t wpb = blockDim.x >> 5;
+  // Shuffles share the MIO pipe with shared memory, so their full chunks move
+  // as coalesced 32-bit rows (row r = one 128-byte access per warp) instead
+  // of 128-bit accesses transposed through shared memory.
+  constexpr bool kDirect = FN == COX_SHFL_IDX || FN == COX_SHFL_UP || FN == COX_SHFL_DOWN || FN == COX_SHFL_XOR;
   for (int64_t c = blockIdx.x * wpb + (threadIdx.x >> 5); c < nchunks; c += gridDim.x * wpb) {
     const int64_t base = c * CH;
     const bool full = c < nfull;
     uint32_t row[kShflRows];
-    if (full) load_rows_full<kShflRows>(in + base, sm, row);
-    else load_rows_tail<kShflRows>(in + base, n - base, 0u, row);
+    if (kDirect && full) {
+#pragma unroll
+      for (int r = 0; r < kShflRows; ++r) row[r] = __ldcs(in + base + r * 32 + lane);
+    } else if (full) {
+      load_rows_full<kShflRows>(in + base, sm, row);
+    } else {
+      load_rows_tail<kShflRows>(in + base, n - base, 0u, row);
+    }
 #pragma unroll
     for (int r = 0; r < kShflRows; ++r) {
       const uint32_t v = row[r];
@@ -55,8 +65,14 @@ __global__ void __launch_bounds__(1024) k_shfl(const uint32_t* __restrict__ in, 
       }
       row[r] = res;
     }
-    if (full) store_rows_full<kShflRows>(out + base, sm, row);
-    else store_rows_tail<kShflRows>(out + base, n - base, row);
+    if (kDirect && full) {
+#pragma unroll
+      for (int r = 0; r < kShflRows; ++r) __stcs(out + base + r * 32 + lane, row[r]);
+    } else if (full) {
+      store_rows_full<kShflRows>(out + base, sm, row);
+    } else {
+      store_rows_tail<kShflRows>(out + base, n - base, row);
+    }
   }
 }
 
