@@ -248,9 +248,11 @@ cox_status cox_coalesced(cox_cgfn fn, cox_dtype dt, int block_dim, const void* d
  * through a warp-aggregated atomic: each coalesced group of keeping lanes
  * gets one contiguous range of d_out from an atomic add on *d_count, and a
  * lane's slot is its group rank in it.  A warp aggregates its 16 rounds of
- * 32 keys, and a CTA its 8 warps, into one atomic.  The ORDER of the ranges is the order in which
- * the atomics landed (not deterministic); the kept keys, their count, and
- * the lane order inside each group are.  d_out: room for n keys; d_count:
+ * 32 keys, and a CTA its 8 warps, into one atomic; a warp packs its kept
+ * keys in shared memory (the compaction's one-pass body) and copies them
+ * out.  The ORDER of the ranges is the order in which the atomics landed
+ * (not deterministic); the kept keys, their count, and the lane order
+ * inside each group are.  d_out: room for n keys; d_count:
  * one int64, zeroed by the call, holds the count when the stream reaches
  * the end of the call.  dt: COX_I32 or COX_U32.  Keys arrive in 16 KB
  * chunks by TMA bulk copies (16-byte aligned d_keys); a copy that does not

@@ -106,16 +106,19 @@ __global__ void __launch_bounds__(256) k_coalesced(int fn, const uint32_t* __res
   }
 }
 
-// filter_arr with warp-aggregated slots.  A warp takes 16 rounds of 32 keys
-// (round j: keys base + 32j + lane); round j's group is its keeping lanes.
-// Group j's range starts after groups 0 .. j-1 of the warp, and a lane's
-// slot is the warp's base + that offset + its rank.  The warps of a CTA
-// aggregate once more: one atomic per CTA per chunk of 8 x 512 keys
-// reserves the warps' totals, and warp w's base follows warps 0 .. w-1.
-// Chunks (16 KB) reach shared memory by TMA bulk copies, one ahead of the
-// one being processed: two slots keep the kernel at 40 registers and 32 KB
-// of shared memory, so six CTAs fit per SM -- more warps to issue from,
-// which this issue-bound kernel needs more than a deeper pipeline.
+// filter_arr with warp-aggregated slots.  A warp owns 512 keys of a chunk;
+// each group of keeping lanes (a ballot per key slot) takes the next
+// popc(ballot) slots of the warp's range, a lane's key landing at the
+// warp's offset + the keeping lanes before it -- the same order as 16
+// rounds of 32 keys each taking its group's slots, computed by the
+// compaction's one-pass body (compact_region), which packs the kept keys
+// in place at the front of the warp's 512 in shared memory.  The warps of
+// a CTA aggregate once more: one atomic per CTA per chunk of 8 x 512 keys
+// reserves the warps' totals, warp w's base follows warps 0 .. w-1, and
+// each warp copies its packed keys out with coalesced stores.  Chunks
+// (16 KB) reach shared memory by TMA bulk copies, one ahead of the one
+// being processed: two slots keep the kernel at 40 registers and 32 KB of
+// shared memory, so six CTAs fit per SM.
 constexpr int kFilterRounds = 16;
 constexpr int kFilterWarps = 8;
 constexpr int kFilterStages = 2;
@@ -124,7 +127,7 @@ constexpr size_t kFilterSmem = (size_t)kFilterStages * kFilterChunk * sizeof(uin
 
 template <bool SIGNED>
 __global__ void __launch_bounds__(32 * kFilterWarps, 6)
-    k_filter_aggregated(const uint32_t* __restrict__ keys, int64_t n, KeepRule rule, uint32_t* __restrict__ out,
+    k_filter_aggregated(const uint32_t* __restrict__ keys, int64_t n, LeRule rule, uint32_t* __restrict__ out,
                         unsigned long long* __restrict__ count, uint32_t limit, unsigned* status, int vec) {
   extern __shared__ __align__(16) uint32_t fbuf[];
   __shared__ __align__(8) uint64_t bar[kFilterStages];
@@ -151,56 +154,48 @@ __global__ void __launch_bounds__(32 * kFilterWarps, 6)
   __syncthreads();
   bool ok = true;
   int64_t it = 0;
+  const int region = wib * (32 * kFilterRounds);  // this warp's keys in a slot
   for (int64_t c = blockIdx.x; c < nch; c += G, ++it) {
-    // slot (it - 1) % stages was read last iteration, before its barriers
+    // slot (it - 1) % stages was last read (copied out) before the barrier
+    // that ended the previous iteration
     if (tid == 0) issue(it + kFilterStages - 1);
     const int par = (int)(it & 1);
-    const int64_t base = c * kFilterChunk + wib * (32 * kFilterRounds);  // this warp's keys
-    uint32_t k[kFilterRounds];
+    const int slot = (int)(it % kFilterStages);
+    uint32_t* buf = fbuf + slot * kFilterChunk;
+    const int valid = (int)min((int64_t)kFilterChunk, n - c * kFilterChunk);  // keys of this chunk
     if (c < nfull) {
-      const int slot = (int)(it % kFilterStages);
       ok = mbar_wait_bounded(bar + slot, (uint32_t)((it / kFilterStages) & 1), limit);
       if (__syncthreads_or(!ok)) {
         ok = false;
         break;
       }
-      const uint32_t* src = fbuf + slot * kFilterChunk + wib * (32 * kFilterRounds);
-#pragma unroll
-      for (int j = 0; j < kFilterRounds; ++j) k[j] = src[32 * j + lane];
-    } else {
-#pragma unroll
-      for (int j = 0; j < kFilterRounds; ++j) {
-        const int64_t i = base + 32 * j + lane;
-        k[j] = i < n ? __ldcs(keys + i) : 0u;
-      }
+    } else {  // a ragged or unaligned chunk: plain loads into the slot
+      for (int i = tid; i < valid; i += 32 * kFilterWarps) buf[i] = __ldcs(keys + c * kFilterChunk + i);
+      __syncthreads();
     }
-    const int rem = (int)max((int64_t)0, min(n - base, (int64_t)(32 * kFilterRounds)));  // this warp's valid keys
-    unsigned m[kFilterRounds];
-    unsigned total = 0;
-#pragma unroll
-    for (int j = 0; j < kFilterRounds; ++j) {
-      m[j] = __ballot_sync(kFull, 32 * j + lane < rem && keep_key<SIGNED>(k[j], rule));
-      total += __popc(m[j]);
-    }
-    if (lane == 0) s_tot[par][wib] = total;
-    fence_proxy_async_smem();  // this thread's reads of the slot, before the refill's async writes
+    // every warp compacts its 512 keys in place (input order), then one
+    // atomic per CTA claims the chunk's output slots
+    const uint32_t kept = compact_region<SIGNED, 32 * kFilterRounds>(buf, region, lane, lt, valid,
+                                                                     valid == kFilterChunk, rule);
+    if (lane == 0) s_tot[par][wib] = kept;
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0) {  // the CTA's slots, and each warp's offset in them (in place of its count)
       unsigned sum = 0;
 #pragma unroll
-      for (int w = 0; w < kFilterWarps; ++w) sum += s_tot[par][w];
+      for (int w = 0; w < kFilterWarps; ++w) {
+        const unsigned t = s_tot[par][w];
+        s_tot[par][w] = sum;
+        sum += t;
+      }
       s_base[par] = sum ? atomicAdd(count, (unsigned long long)sum) : 0ull;
     }
     __syncthreads();
-    unsigned long long b = s_base[par];
-    for (int w = 0; w < wib; ++w) b += s_tot[par][w];
-    uint32_t* o = out + b;  // this warp's range
-    unsigned off = 0;
-#pragma unroll
-    for (int j = 0; j < kFilterRounds; ++j) {
-      if (m[j] & (1u << lane)) o[off + __popc(m[j] & lt)] = k[j];
-      off += __popc(m[j]);
-    }
+    uint32_t* o = out + (s_base[par] + s_tot[par][wib]);
+    const uint32_t* src = buf + region;
+#pragma unroll 4
+    for (int i = lane; i < (int)kept; i += 32) o[i] = src[i];
+    fence_proxy_async_smem();  // this thread's accesses to the slot, before the bulk copy that refills it
+    __syncthreads();
   }
   if (!ok && tid == 0) {  // a copy did not land in time: record it, give the copies in flight a bounded wait
     atomicOr(status, (unsigned)kDevTimeout);
@@ -236,7 +231,7 @@ static cox_status launch_filter(const void* d_keys, int64_t n, int64_t threshold
   }
   const int64_t ctas = (n + kFilterChunk - 1) / kFilterChunk;
   k<<<(int)(ctas < g ? ctas : g), 32 * kFilterWarps, kFilterSmem, st>>>(
-      static_cast<const uint32_t*>(d_keys), n, keep_rule<SIGNED>(threshold), static_cast<uint32_t*>(d_out),
+      static_cast<const uint32_t*>(d_keys), n, le_rule<SIGNED>(threshold), static_cast<uint32_t*>(d_out),
       reinterpret_cast<unsigned long long*>(d_count), spin_limit(), device_status_word(), aligned16(d_keys) ? 1 : 0);
   return launch_status();
 }
