@@ -466,8 +466,10 @@ __global__ void __launch_bounds__(256, 4) k_band_walk_vec(const void* __restrict
 template <int DT>
 struct StripCfg {
   static constexpr int EB = DT == COX_U8 ? 1 : 4;
-  static constexpr int RB = 8;                        // rows per stage (multiple of 4, divides 32)
-  static constexpr int NS = DT == COX_U8 ? 12 : 5;    // ring stages per team
+  // rows per stage (multiple of 4, divides 32): 8-bit stages are cheap, so
+  // they take 16 rows to halve the per-stage hand-offs between the warps
+  static constexpr int RB = DT == COX_U8 ? 16 : 8;
+  static constexpr int NS = DT == COX_U8 ? 6 : 5;     // ring stages per team (shared memory allows no more)
   static constexpr int NP = 7;                        // warp teams per CTA
   static constexpr int HL = 32 / RB;                  // lanes per row in the scans across lanes
   static constexpr int SBP = RB + 4;                  // transpose row pitch (words)
@@ -531,7 +533,7 @@ __device__ __forceinline__ void strip_add_prefixes(const uint8_t* stage, int r, 
 // Tagged A word: value in the low half, kATag in the high half once written
 // (the words are zeroed before the launch).
 constexpr uint32_t kATag = 1u;
-constexpr int kClGroup = 4;  // left-strip words a lane loads per round trip
+constexpr int kClGroup = 8;  // left-strip words a lane loads per round trip
 
 __device__ __forceinline__ uint64_t ld_relaxed_u64g(const unsigned long long* p) {
   uint64_t v;
